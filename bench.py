@@ -1,0 +1,514 @@
+#!/usr/bin/env python3
+"""Headline benchmark: exact triangle counting on R-MAT scale 22.
+
+One step = one pass of the whole method over the graph: build the oriented
+CSR and its partition (tc_build_oriented_csr) and count the total and every
+per-vertex count (tc_count), inputs resident in HBM.  The metric is input
+undirected edges per second.
+
+Workload (default): R-MAT scale 22, edge factor 16, (a, b, c, d) =
+(0.57, 0.19, 0.19, 0.05), seeded relabelling, symmetrised, de-duplicated,
+self-loops dropped (about 4.19M vertices, 64.2M undirected edges), int64
+row_ptr + int32 col.  The input CSR (547 MB) and the oriented CSR exceed the
+129 MB L2, so no explicit L2 flush is done between steps.
+
+Other workloads (``--workload``): grid4096, er1024, ba_batch4096 (one batched
+pass vs one launch per graph), serve (Poisson request stream through
+tc_submit/tc_poll, p50/p99 latency).
+
+``--impl reference`` times the CPU oracle (the paper's sequential forward
+algorithm, written here as plain C) on the host cores, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+# ----------------------------------------------------------------------------- helpers
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_graph(name, seed):
+    from paper_1804_06926_gb300 import gen
+    if name == "rmat22":
+        return gen.rmat(22, 16, seed=seed), "R-MAT s22 ef16 (0.57,0.19,0.19,0.05)"
+    if name == "grid4096":
+        return gen.grid(4096, 4096, seed=seed), "grid 4096x4096 + diag p=0.3 + 1% long-range"
+    if name == "er1024":
+        return gen.er(1024, 8192, seed=seed), "Erdos-Renyi G(1024, 8192)"
+    raise KeyError(name)
+
+
+def oriented_out_degrees(g):
+    """d+(x) from the rank order (d, id); bookkeeping for the byte model."""
+    deg = np.diff(g.row_ptr).astype(np.int64)
+    u = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    v = g.col.astype(np.int64)
+    keep = (deg[u] < deg[v]) | ((deg[u] == deg[v]) & (u < v))
+    return np.bincount(u[keep], minlength=g.n).astype(np.int64), deg
+
+
+def algorithmic_bytes(g, per_vertex=True):
+    """Bytes the per-edge intersection must read by definition (both sorted
+    lists of every oriented edge) plus compulsory structure and output traffic:
+    4*sum_{(u,v) in E+}(d+(u)+d+(v)) + 4|E+| + 8(n+1) + 8n[per-vertex] + 8.
+    sum_{E+}(d+(u)+d+(v)) = sum_x d+(x) * d(x) (x is the source of d+(x) edges
+    and the target of d(x)-d+(x) edges, each contributing d+(x))."""
+    dplus, deg = oriented_out_degrees(g)
+    s = int((dplus * deg).sum())
+    m = g.m
+    b = 4 * s + 4 * m + 8 * (g.n + 1) + (8 * g.n if per_vertex else 0) + 8
+    return b, s, dplus, deg
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.rows = []
+        self.proc = None
+        self.uuid = device_uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.25)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def device_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_tag):
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
+    if that summary was taken on the current source of the count kernels."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.ncu.txt")
+    src = os.path.join(ROOT, "paper_1804_06926_gb300", "csrc", "tc_count.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = {}
+        for line in open(path):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256_16") != sha:
+            return None
+        return float(kv["dram_bytes_per_launch_fullsize"])
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_rate(g, target_work=4e9, label=""):
+    """Time the CPU oracle on a bounded sample: orientation of the full graph,
+    then the forward count over every k-th source row; extrapolate to the whole
+    graph by merge work.  Returns (edges/s, description, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    rpp, colp = oracle.orient(g.n, g.row_ptr, g.col)
+    t_orient = time.perf_counter() - t0
+    dplus = np.diff(rpp)
+    # merge work of row u: sum_{v in N+(u)} (d+(u) + d+(v))
+    src = np.repeat(np.arange(g.n, dtype=np.int64), dplus)
+    w_edge = dplus[src] + dplus[colp.astype(np.int64)]
+    w_row = np.bincount(src, weights=w_edge, minlength=g.n)
+    W = float(w_row.sum())
+    stride = max(1, int(W / target_work)) if W > 0 else 1
+    w_sample = float(w_row[::stride].sum())
+    t1 = time.perf_counter()
+    oracle.count_rows(g.n, rpp, colp, 0, g.n, stride)
+    t_sample = time.perf_counter() - t1
+    frac = w_sample / W if W else 1.0
+    t_full = t_orient + (t_sample / frac if frac > 0 else 0.0)
+    desc = (f"{label}oracle orientation of the full graph ({t_orient:.2f} s) + forward count over every "
+            f"{stride}th source row ({100 * frac:.1f}% of the merge work, {t_sample:.2f} s), "
+            f"extrapolated by merge work to {t_full:.1f} s for the whole graph; 1 thread")
+    return g.m / t_full, desc, t_orient + t_sample
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_rmat_like(args, torch, binding, dev, rank, world):
+    name = args.workload
+    g, desc = workload_graph(name, seed=rank)
+    log(f"[rank {rank}] {desc}: n={g.n} m={g.m}")
+    B_alg, S, dplus, deg = algorithmic_bytes(g, per_vertex=True)
+    ctx = binding.Context(dev.index)
+    stream = torch.cuda.current_stream()
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    total = torch.zeros(1, dtype=torch.int64, device=dev)
+    pv = torch.zeros(g.n, dtype=torch.int64, device=dev)
+
+    def step():
+        o = ctx.build(g.n, rp, col, stream=stream)
+        ctx.count(o, total, pv, stream=stream)
+        o.release(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    T_gpu = int(total.item())
+    pv_sum = int(pv.sum().item())
+    assert pv_sum == 3 * T_gpu, "per-vertex counts do not sum to 3T"
+
+    sampler = ClockSampler(device_uuid(torch, dev))
+    sampler.start()
+    ctx.read_trace()  # reset
+    ctx.set_trace(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = e0.elapsed_time(e1)
+    ctx.set_trace(False)
+    tr = ctx.read_trace()
+    clocks = sampler.stop()
+    ms = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    ph = {k: v / args.steps for k, v in tr["phase_ms"].items()}
+    count_ms = ph["count_small"] + ph["count_warp"] + ph["count_cta"]
+    build_ms = sum(ph[k] for k in ("degree", "orient_count", "orient_scan", "orient_scatter", "pivot_count",
+                                   "pivot_scan", "pivot_scatter", "items"))
+
+    # end to end through the public API: pinned host CSR in, host results out
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_col = torch.from_numpy(g.col).pin_memory()
+    h_tot = torch.zeros(1, dtype=torch.int64).pin_memory()
+    h_pv = torch.zeros(g.n, dtype=torch.int64).pin_memory()
+
+    def e2e_step():
+        o = ctx.build(g.n, h_rp, h_col, stream=stream)
+        ctx.count(o, h_tot, h_pv, stream=stream)  # host outputs: copies back and synchronises
+        o.release(stream)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 3)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    assert int(h_tot[0]) == T_gpu
+    h2d = 8 * (g.n + 1) + 4 * g.nnz
+    d2h = 8 + 8 * g.n
+
+    peak, peak_kind = peaks()
+    achieved = B_alg / (count_ms * 1e-3) / 1e9 if count_ms > 0 else None
+    traffic = profiled_traffic(f"tc_count_{name}")
+    units = g.m * world
+    res = {
+        "metric": "edges/s (undirected input edges, build + count per step)",
+        "value": units / (ms * 1e-3),
+        "unit": "edges/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32 ids / int64 counts",
+        "data": "synthetic (seeded generator; the paper's SNAP/DIMACS graphs are not available)",
+        "config": {"workload": desc, "n": g.n, "m_undirected": g.m, "per_vertex": True,
+                   "l2": "no flush: input CSR %.0f MB > 129 MB L2" % ((8 * (g.n + 1) + 4 * g.nnz) / 1e6),
+                   "seed": rank, "parallelism": "replicas only (one graph per GPU)" if world > 1 else "1 GPU"},
+        "triangles": T_gpu,
+        "phases_ms": {k: round(v, 4) for k, v in ph.items() if v > 0},
+        "build_ms": build_ms,
+        "count_ms": count_ms,
+        "roofline": {"bound": "hbm", "kernel": "tc_count (k_count_small + k_count_warp + k_count_cta)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "algorithmic_bytes": B_alg, "sum_dplus_u_plus_dplus_v": S},
+        "e2e": {"value": units / e2e_s, "unit": "edges/s", "ms_per_step": e2e_s * 1e3,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(tr["launches"]),
+        "clocks": clocks,
+    }
+    return res, g
+
+
+def run_batch(args, torch, binding, dev, rank, world):
+    """4096 Barabasi-Albert graphs: one batched pass (CUDA-graph plan) against
+    one build + count per graph, identical counts."""
+    from paper_1804_06926_gb300 import gen
+    G = args.batch_graphs
+    b = gen.ba_batch(G, 100, 20000, 2, 16, seed0=rank * G)
+    m_tot = int(b.edge_off[-1] // 2)
+    log(f"[rank {rank}] BA batch: G={G} n={int(b.vtx_off[-1])} m={m_tot}")
+    ctx = binding.Context(dev.index)
+    vo, eo, rp, col = (torch.from_numpy(x).to(dev) for x in (b.vtx_off, b.edge_off, b.row_ptr, b.col))
+    totals = torch.zeros(G, dtype=torch.int64, device=dev)
+    pv = torch.zeros(int(b.vtx_off[-1]), dtype=torch.int64, device=dev)
+    plan = ctx.batch_plan(vo, eo, rp, col, totals, pv)
+    for _ in range(args.warmup):
+        plan.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(device_uuid(torch, dev))
+    sampler.start()
+    e0.record()
+    for _ in range(args.steps):
+        plan.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms_batch = e0.elapsed_time(e1) / args.steps
+    T_batch = totals.cpu().numpy().copy()
+    # one launch sequence per graph
+    graphs = [b.graph(i) for i in range(G)]
+    dev_graphs = [(gg.n, torch.from_numpy(gg.row_ptr).to(dev), torch.from_numpy(gg.col).to(dev)) for gg in graphs]
+    tot1 = torch.zeros(G, dtype=torch.int64, device=dev)
+    pvs = [torch.zeros(gg.n, dtype=torch.int64, device=dev) for gg in graphs]
+
+    def per_graph():
+        for i, (n, r, c) in enumerate(dev_graphs):
+            o = ctx.build(n, r, c)
+            ctx.count(o, tot1[i:i + 1], pvs[i])
+            o.release(None)
+
+    per_graph()
+    torch.cuda.synchronize()
+    reps = max(1, args.steps // 10)
+    e0.record()
+    for _ in range(reps):
+        per_graph()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1) / reps
+    assert np.array_equal(tot1.cpu().numpy(), T_batch), "batched counts differ from per-graph counts"
+    res = {
+        "metric": "graphs/s and edges/s (4096 BA graphs per batch, build + count)",
+        "value": m_tot / (ms_batch * 1e-3), "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 ids / int64 counts", "data": "synthetic",
+        "config": {"workload": f"BA batch G={G}, n~U[100,20000], k~U[2,16]", "m_undirected": m_tot,
+                   "l2": "no flush: batch CSR %.0f MB > 129 MB L2" % ((b.row_ptr.nbytes + b.col.nbytes) / 1e6)},
+        "graphs_per_s": G / (ms_batch * 1e-3),
+        "one_launch_per_graph": {"ms": ms_single, "edges_per_s": m_tot / (ms_single * 1e-3),
+                                 "graphs_per_s": G / (ms_single * 1e-3)},
+        "batch_speedup": ms_single / ms_batch,
+        "triangles_total": int(T_batch.sum()),
+        "clocks": clocks,
+    }
+    return res, None
+
+
+def run_serve(args, torch, binding, dev, rank, world):
+    """Poisson request stream mixing R-MAT scales 10..20 and BA graphs, through
+    tc_submit / tc_poll with a 40 GB budget; latency percentiles and edges/s."""
+    from paper_1804_06926_gb300 import gen
+    rng = np.random.default_rng(args.seed)
+    pool = []
+    for i in range(args.serve_pool):
+        if rng.random() < 0.5:
+            pool.append(gen.rmat(int(rng.integers(10, 21)), 16, seed=int(rng.integers(1 << 30))))
+        else:
+            pool.append(gen.ba(int(rng.integers(100, 20001)), int(rng.integers(2, 17)), seed=int(rng.integers(1 << 30))))
+    srv = binding.Server(device=dev.index, slots=args.slots, hbm_budget_bytes=40 << 30)
+    # closed-loop capacity first, then an open-loop Poisson stream at ~0.7x of it
+    t0 = time.perf_counter()
+    tks = [srv.submit(g.n, g.row_ptr, g.col) for g in pool]
+    for t in tks:
+        srv.wait(t, 600000)
+        srv.release(t)
+    cap_rps = len(pool) / (time.perf_counter() - t0)
+    rate = args.serve_rate or 0.7 * cap_rps
+    nreq = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    picks = rng.integers(0, len(pool), nreq)
+    lat, edges = [], 0
+    tickets = []
+    start = time.perf_counter()
+    for i in range(nreq):
+        now = time.perf_counter() - start
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        g = pool[picks[i]]
+        key = int(picks[i]) + 1 if args.serve_cache else 0
+        tickets.append((srv.submit(g.n, g.row_ptr, g.col, key=key), g.m))
+    for t, m in tickets:
+        r = srv.wait(t, 600000)
+        assert r["status"] == 0
+        lat.append(r["latency_ms"])
+        edges += m
+        srv.release(t)
+    wall = time.perf_counter() - start
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    res = {
+        "metric": "served count requests: edges/s, p50/p99 latency", "value": edges / wall, "unit": "edges/s",
+        "n_gpus": world, "steps": nreq, "warmup": len(pool), "ms_per_step": wall * 1e3 / nreq,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids / int64 counts",
+        "data": "synthetic", "config": {"workload": f"{nreq} Poisson requests at {rate:.1f}/s over a pool of "
+                                                    f"{len(pool)} graphs (R-MAT s10-20 / BA), 40 GB budget, "
+                                                    f"{args.slots} slots, cache={'on' if args.serve_cache else 'off'}"},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "closed_loop_capacity_rps": cap_rps, "server_stats": st,
+    }
+    return res, None
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "grid4096", "er1024", "ba_batch4096", "serve"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rate", type=float, default=0.0)
+    ap.add_argument("--serve-cache", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        g, desc = workload_graph(args.workload if args.workload in ("rmat22", "grid4096", "er1024") else "rmat22", 0)
+        rates = []
+        for i in range(args.warmup + args.steps):
+            r, d, secs = oracle_rate(g, target_work=2e8)
+            if i >= args.warmup:
+                rates.append(r)
+        v = statistics.median(rates)
+        line = {"impl": "reference", "metric": "edges/s (undirected input edges, build + count per step)",
+                "value": v, "unit": "edges/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": g.m / v * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32 ids / int64 counts", "data": "synthetic",
+                "config": {"workload": desc, "n": g.n, "m_undirected": g.m},
+                "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": d},
+                "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1804_06926_gb300 import _build, binding
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    binding.load(build_if_missing=False)
+
+    if args.workload == "ba_batch4096":
+        res, g = run_batch(args, torch, binding, dev, rank, world)
+    elif args.workload == "serve":
+        res, g = run_serve(args, torch, binding, dev, rank, world)
+    else:
+        res, g = run_rmat_like(args, torch, binding, dev, rank, world)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and g is not None:
+        v, d, _ = oracle_rate(g)
+        res["cpu_baseline"] = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": d}
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * tc.h -- C ABI of the GB300-native exact triangle counter.
+ *
+ * Method (Wang, Wang, Yang, Owens, "A Comparative Study on Exact Triangle
+ * Counting Algorithms on the GPU", HPGP'16), Sec. 3.2 "TC using Set
+ * Intersection", Alg. 2, and Sec. 4.2 (its implementation):
+ *   1. Form the filtered edge list: keep every undirected edge once, oriented
+ *      from the lower to the higher rank, rank(v) = (d(v), v)  (Sec. 4.2.1);
+ *   2. compact the kept edges into an oriented CSR, the induced subgraph of
+ *      Sec. 4.2.1: N+(u) = { v : {u,v} in E, rank(u) < rank(v) }, ascending;
+ *   3. partition the oriented edges by list size (Alg. 2 Partition, Sec. 4.2.2
+ *      dynamic grouping) and intersect N+(u) with N+(v) for every oriented
+ *      edge (u, v); each common w closes triangle {u, v, w} (Sec. 3.2);
+ *   4. reduce the intersection sizes to the total (Alg. 2 Reduce) and, on
+ *      request, to per-vertex counts t(v) = number of triangles containing v.
+ * Results are exact int64 integers; there is exactly one correct answer.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns tc_status; nothing throws across the ABI.  On an
+ *     error, tc_last_error(ctx) holds a one-line reason.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued asynchronously on it unless a call says it
+ *     synchronises; device results are valid once the stream reaches them.
+ *   - Input buffers are borrowed for the duration of the call (for device
+ *     inputs: until the enqueued work has read them).  Output buffers are
+ *     owned by the caller.  tc_ocsr and tc_server handles are owned by the
+ *     library and freed by the caller with tc_ocsr_free / tc_server_destroy.
+ *   - Vertex ids are int32 (n < 2^31); offsets are int64.
+ *   - Library-owned device memory comes from the device's stream-ordered
+ *     memory pool (cudaMallocAsync on the call's stream).
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tc_status {
+    TC_OK = 0,
+    TC_PENDING = 1,              /* tc_poll: request not finished yet */
+    TC_ERR_INVALID_ARG = -1,     /* NULL handle, negative size, bad flag combination */
+    TC_ERR_INVALID_GRAPH = -2,   /* TC_VALIDATE found a non-simple / asymmetric / unsorted CSR, or an id outside [0,n) */
+    TC_ERR_OOM = -3,             /* device allocation failed */
+    TC_ERR_BUDGET = -4,          /* serving: request larger than the whole HBM budget */
+    TC_ERR_TIMEOUT = -5,         /* a bounded wait gave up */
+    TC_ERR_CUDA = -6,            /* any other CUDA runtime error (message in tc_last_error) */
+    TC_ERR_NOT_FOUND = -7        /* serving: unknown ticket */
+} tc_status;
+
+/* tc_graph.flags / tc_batch.flags */
+#define TC_IN_DEVICE     0x0u  /* input pointers are device memory (default) */
+#define TC_IN_HOST       0x1u  /* input pointers are host memory; the call copies them to the device */
+#define TC_VALIDATE      0x2u  /* check a CSR input (sorted, no loops, no duplicates, symmetric, ids in range);
+                                  synchronises the stream once to read the verdict */
+
+/* An undirected simple graph, as the paper states the problem (Sec. 3):
+ *   CSR form   (row_ptr != NULL): row_ptr[n+1] (int64, row_ptr[0] = 0,
+ *              row_ptr[n] = nnz), col[nnz] (int32), both directions of every
+ *              edge present, each row strictly ascending, no self-loops.
+ *              nnz = 2m.
+ *   Edge list  (row_ptr == NULL): src[nnz], dst[nnz] pairs.  Self-loops,
+ *              duplicates and either or both directions are allowed; they
+ *              are dropped and symmetrised (the paper's dataset treatment,
+ *              Table 1 caption).  Ids outside [0, n) give TC_ERR_INVALID_GRAPH. */
+typedef struct tc_graph {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int32_t* src;
+    const int32_t* dst;
+    uint32_t flags;
+} tc_graph;
+
+/* Tuning knobs (Alg. 2 Partition thresholds; the paper leaves them open,
+ * Sec. 4.2.2).  Zero means "use the built-in default".  No knob changes a
+ * result, only the speed. */
+typedef struct tc_config {
+    int32_t small_max;     /* oriented edges with max(d+(u), d+(v)) <= small_max are merged by one
+                              thread each (the paper's TwoSmall); default 8 */
+    int32_t warp_max;      /* pivots with d+ <= warp_max probe a warp-private table; larger pivots a
+                              CTA-wide table (the paper's TwoLarge role); default 64 */
+    int32_t table_cap;     /* keys per CTA table segment (power of two, <= 8192); longer lists are
+                              split into segments; default 2048 */
+    int32_t probe;         /* 0/1 = open-addressing hash probe, 2 = binary search of the sorted list */
+    int32_t cta_threads;   /* threads per CTA of the CTA-table kernel (128..1024); default 512 */
+    int32_t chunk;         /* partners per work item; default 256 */
+    int32_t reserved[10];
+} tc_config;
+
+typedef struct tc_ctx tc_ctx;
+typedef struct tc_ocsr tc_ocsr;
+
+/* Tracing: CUDA events around each phase, recorded on the stream the phase
+ * runs on, plus a count of the library's kernel launches.  Off by default;
+ * never active inside a CUDA-graph capture. */
+#define TC_TRACE_PHASES 16
+enum {
+    TC_PH_DEGREE = 0, TC_PH_VALIDATE, TC_PH_ORIENT_COUNT, TC_PH_ORIENT_SCAN, TC_PH_ORIENT_SCATTER,
+    TC_PH_PIVOT_COUNT, TC_PH_PIVOT_SCAN, TC_PH_PIVOT_SCATTER, TC_PH_ITEMS, TC_PH_COUNT_SMALL,
+    TC_PH_COUNT_WARP, TC_PH_COUNT_CTA, TC_PH_EDGE_SORT, TC_PH_COUNT_INIT
+};
+typedef struct tc_trace {
+    int64_t launches;                        /* kernel launches since the last read */
+    double phase_ms[TC_TRACE_PHASES];        /* summed device time per phase */
+    int32_t phase_calls[TC_TRACE_PHASES];    /* event pairs summed per phase */
+} tc_trace;
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * cfg may be NULL (all defaults).  Cheap; holds no graph memory. */
+tc_status tc_ctx_create(int device, const tc_config* cfg, tc_ctx** out);
+void tc_ctx_destroy(tc_ctx* ctx);
+/* One-line description of the last error on this context ("" if none). */
+const char* tc_last_error(const tc_ctx* ctx);
+/* Replace the tuning knobs (same meaning as in tc_ctx_create). */
+tc_status tc_ctx_set_config(tc_ctx* ctx, const tc_config* cfg);
+tc_status tc_ctx_get_config(const tc_ctx* ctx, tc_config* out);
+/* Turn phase tracing on (1) or off (0). */
+tc_status tc_ctx_set_trace(tc_ctx* ctx, int enable);
+/* Wait for the recorded events, sum them into *out and reset the trace. */
+tc_status tc_ctx_read_trace(tc_ctx* ctx, tc_trace* out);
+
+/* Steps 1-3 of the method (Sec. 4.2.1 edge-list filtering and induced
+ * subgraph; Alg. 2 Partition): from an undirected graph, build on the device
+ * the oriented CSR N+ and the work partition that tc_count consumes.
+ * Asynchronous on `stream` (no host synchronisation) for a CSR input without
+ * TC_VALIDATE; an edge-list input synchronises once (to learn the number of
+ * distinct edges), and so does TC_VALIDATE (to read the verdict).  *out receives a
+ * library-owned handle; free it with tc_ocsr_free after the last tc_count on
+ * it has completed. */
+tc_status tc_build_oriented_csr(tc_ctx* ctx, const tc_graph* g, tc_ocsr** out, void* stream);
+
+/* Steps 3-4 (Sec. 3.2 intersection, Alg. 2 Compute_Intersection and
+ * Reduce): total = number of triangles; per_vertex[v] = t(v) when
+ * per_vertex != NULL (n entries).  Both may be device or host pointers:
+ * device outputs are written asynchronously; if either is host memory the
+ * call copies the results back and synchronises `stream` before returning.
+ * Any number of tc_count calls may run on one tc_ocsr, on any streams. */
+tc_status tc_count(tc_ctx* ctx, const tc_ocsr* o, int64_t* total, int64_t* per_vertex, void* stream);
+
+/* Read-only view of a built oriented CSR (device pointers, owned by the handle). */
+typedef struct tc_ocsr_view {
+    int64_t n;                 /* vertices */
+    int64_t m;                 /* |E+| = undirected edges */
+    const int64_t* row_ptr;    /* device [n+1]: N+(u) = col[row_ptr[u] .. row_ptr[u+1]) */
+    const int32_t* col;        /* device [m], ascending within a row */
+    int64_t bytes;             /* device bytes held by the handle */
+} tc_ocsr_view;
+tc_status tc_ocsr_get_view(const tc_ocsr* o, tc_ocsr_view* out);
+/* Copy the oriented CSR (Sec. 4.2.1 induced subgraph) into caller buffers
+ * row_ptr[n+1] and col[m], host or device memory; synchronises `stream`. */
+tc_status tc_ocsr_copy(const tc_ocsr* o, int64_t* row_ptr, int32_t* col, void* stream);
+/* Free the handle's device memory; synchronises the device first. */
+void tc_ocsr_free(tc_ocsr* o);
+/* Free in stream order (no host synchronisation): every use of the handle
+ * must already be enqueued on `stream` or ordered before it. */
+void tc_ocsr_release(tc_ocsr* o, void* stream);
+
+/* A batch of G independent graphs (no counterpart in the paper, which counts
+ * one graph at a time; each graph is the problem of Sec. 3).  Graph i has
+ * n_i = vtx_off[i+1]-vtx_off[i] vertices and nnz_i = edge_off[i+1]-edge_off[i]
+ * CSR entries; row_ptr[sum n_i + 1] holds offsets into the concatenated col
+ * array, and col holds LOCAL ids in [0, n_i).  All four arrays are device
+ * memory, or host memory with TC_IN_HOST.  Each graph must be a valid CSR as
+ * in tc_graph (TC_VALIDATE checks it). */
+typedef struct tc_batch {
+    int64_t G;
+    const int64_t* vtx_off;    /* [G+1] */
+    const int64_t* edge_off;   /* [G+1] */
+    const int64_t* row_ptr;    /* [vtx_off[G]+1] */
+    const int32_t* col;        /* [edge_off[G]] */
+    uint32_t flags;
+} tc_batch;
+
+/* Count every graph of the batch in one pass of the pipeline over their
+ * disjoint union: totals[i] = triangles of graph i (G entries);
+ * per_vertex[vtx_off[i] + v] = t(v) of graph i when per_vertex != NULL.
+ * Output placement and synchronisation as in tc_count. */
+tc_status tc_count_batch(tc_ctx* ctx, const tc_batch* b, int64_t* totals, int64_t* per_vertex, void* stream);
+
+/* Capture the whole batch pipeline (build + count) once into a CUDA graph and
+ * replay it: for repeated batches of the same shape (same G, offsets and
+ * sizes; contents of row_ptr/col may change in place).  The first call
+ * captures and replays; later calls with the same plan replay only.  All
+ * pointers must be device memory and stay valid while the plan lives. */
+typedef struct tc_batch_plan tc_batch_plan;
+tc_status tc_batch_plan_create(tc_ctx* ctx, const tc_batch* b, int64_t* totals, int64_t* per_vertex,
+                               void* stream, tc_batch_plan** out);
+tc_status tc_batch_plan_launch(tc_batch_plan* plan, void* stream);
+void tc_batch_plan_destroy(tc_batch_plan* plan);
+
+/* ---- serving: continuous batching of count requests ----------------------
+ * A server owns a request thread, `slots` CUDA streams and an HBM budget.
+ * tc_submit copies the request's host arrays, queues it and returns at once
+ * with a ticket.  The request thread admits queued requests in arrival order
+ * while a slot is free and the bytes of resident oriented CSRs plus the
+ * request's estimate fit the budget, builds the oriented CSR on the slot's
+ * stream, counts it, and retires it when its stream is done; requests that
+ * arrive while others are on the GPU overlap with them.  Oriented CSRs of
+ * retired requests stay resident (keyed by the caller's graph_key, LRU
+ * eviction under the budget), so a repeated key skips the build.
+ * Results are exact and identical whether a request runs alone or in a mix. */
+typedef struct tc_server tc_server;
+typedef struct tc_server_config {
+    int32_t device;
+    int32_t slots;             /* concurrent requests on the GPU (streams); default 8 */
+    int64_t hbm_budget_bytes;  /* default 40 GiB */
+    int32_t per_vertex;        /* 1 = also return t(v) */
+    int32_t reserved[7];
+} tc_server_config;
+
+typedef struct tc_result {
+    tc_status status;          /* TC_OK, TC_PENDING or an error */
+    int64_t total;
+    int64_t n;                 /* length of per_vertex */
+    const int64_t* per_vertex; /* host memory owned by the server; valid until the ticket is released */
+    double submit_to_done_ms;  /* latency: tc_submit -> result ready on the host */
+    double queue_ms;           /* time spent waiting for admission */
+    int32_t cache_hit;         /* 1 if the oriented CSR was resident */
+} tc_result;
+
+tc_status tc_server_create(const tc_server_config* cfg, const tc_config* tuning, tc_server** out);
+/* Stops the request thread after finishing admitted work; frees everything. */
+void tc_server_destroy(tc_server* s);
+/* g must be a host-memory CSR (flags may include TC_VALIDATE); graph_key != 0
+ * names the graph for the resident cache (0 = do not cache). */
+tc_status tc_submit(tc_server* s, const tc_graph* g, uint64_t graph_key, uint64_t* ticket);
+/* Non-blocking.  TC_PENDING until done; then the result (and its status). */
+tc_status tc_poll(tc_server* s, uint64_t ticket, tc_result* out);
+/* Block until the ticket is done or timeout_ms elapses (TC_ERR_TIMEOUT). */
+tc_status tc_wait(tc_server* s, uint64_t ticket, int64_t timeout_ms, tc_result* out);
+/* Forget a finished ticket and free its host result. */
+tc_status tc_release(tc_server* s, uint64_t ticket);
+/* Counters: requests admitted, finished, cache hits, bytes resident. */
+typedef struct tc_server_stats {
+    int64_t submitted, admitted, finished, cache_hits, evictions;
+    int64_t resident_bytes, peak_inflight_bytes;
+    int32_t peak_inflight;
+} tc_server_stats;
+tc_status tc_server_get_stats(const tc_server* s, tc_server_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H */

@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -28,10 +29,17 @@ _vp, _i64 = ctypes.c_void_p, ctypes.c_int64
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, single thread, portable flags)."""
     src = os.path.join(_HERE, "tc_oracle.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+    stamp = _SO + ".arch"
+    try:
+        arch_ok = open(stamp).read().strip() == platform.machine()
+    except OSError:
+        arch_ok = False
+    if force or not arch_ok or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, src])
         os.replace(tmp, _SO)
+        with open(stamp, "w") as f:
+            f.write(platform.machine() + "\n")
     return _SO
 
 

@@ -1,0 +1,123 @@
+// tc_internal.cuh -- shared declarations of the CUDA path (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+constexpr int kWarp = 32;
+
+// Device-side counters of one oriented CSR (written by the build, read by the
+// count kernels).
+struct DevCounters {
+    unsigned long long n_items_warp;   // work items of the warp-table class
+    unsigned long long n_items_cta;    // work items of the CTA-table class
+    unsigned long long n_pivot_edges;  // oriented edges assigned to a pivot
+    unsigned long long n_small_edges;  // oriented edges merged thread-per-edge
+    int error;                         // validation verdict (0 = ok)
+    int max_dplus;                     // max out-degree after orientation
+};
+
+// One unit of pivot work: intersect the pivot's list segment
+// N+(p)[seg*cap .. seg*cap+cap) with N+(q) for the partners q in
+// pcol[prp[p]+pb .. prp[p]+pe).
+struct __align__(16) Item {
+    int p, seg, pb, pe;
+};
+
+struct Tuning {
+    int small_max = 8;
+    int warp_max = 64;
+    int table_cap = 2048;
+    int probe = 1;          // 1 hash, 2 binary search
+    int cta_threads = 512;
+    int chunk = 256;
+};
+
+}  // namespace tc
+
+// Library-owned oriented CSR and its work partition.
+struct tc_ocsr {
+    int device = 0;
+    int64_t n = 0, m = 0;
+    int64_t* rpp = nullptr;     // [n+1] oriented row offsets
+    int32_t* colp = nullptr;    // [m]
+    int32_t* dplus = nullptr;   // [n] out-degrees
+    int64_t* prp = nullptr;     // [n+1] partner row offsets
+    int32_t* pcol = nullptr;    // [m] partners (only the first n_pivot_edges used)
+    tc::Item* items_warp = nullptr;
+    tc::Item* items_cta = nullptr;
+    int64_t items_warp_cap = 0, items_cta_cap = 0;
+    tc::DevCounters* dc = nullptr;
+    // batch mode: vertex -> graph id and the number of graphs
+    int32_t* row_graph = nullptr;
+    int64_t G = 0;
+    tc::Tuning tun;             // thresholds the partition was built with
+    int64_t bytes = 0;
+};
+
+struct tc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    tc::Tuning tun;
+    std::string err;
+    // tracing: kernel launches issued, and CUDA-event pairs per phase
+    bool trace = false;
+    long long launches = 0;
+    struct Rec { int phase; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace tc {
+
+// Phase ids of the trace (tc_trace.phase_ms index).
+enum Phase {
+    kPhDegree = 0, kPhValidate, kPhOrientCount, kPhOrientScan, kPhOrientScatter, kPhPivotCount, kPhPivotScan,
+    kPhPivotScatter, kPhItems, kPhCountSmall, kPhCountWarp, kPhCountCta, kPhEdgeSort, kPhCountInit, kNumPhases
+};
+
+// RAII phase marker: records an event pair on `s` when tracing is on.
+struct PhaseScope {
+    tc_ctx* c;
+    int id;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    PhaseScope(tc_ctx* c_, int id_, cudaStream_t s_);
+    ~PhaseScope();
+};
+#define TC_LAUNCH(ctx) ((ctx)->launches++)
+
+// status helpers
+tc_status set_err(tc_ctx* ctx, tc_status st, const std::string& msg);
+tc_status cuda_err(tc_ctx* ctx, cudaError_t e, const char* where);
+
+// stream-ordered allocation from the device pool
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// device-wide exclusive scan: out[0..n] (n+1 entries) of int32 in[0..n)
+cudaError_t scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* tmp, size_t tmp_bytes,
+                            cudaStream_t s);
+size_t scan_tmp_bytes(int64_t n);
+
+// Build the oriented CSR and its partition from a device CSR (rows may be a
+// batch: row_graph/vtx_off non-null map local neighbour ids to global ones).
+tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                const int32_t* col, const int64_t* vtx_off, int64_t G,
+                                bool validate, tc_ocsr** out, cudaStream_t s);
+
+// Canonicalise a device edge list into a device CSR (library-owned buffers).
+tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t npairs, const int32_t* src, const int32_t* dst,
+                       int64_t** row_ptr, int32_t** col, int64_t* nnz, cudaStream_t s);
+
+// Launch the count kernels.  totals: device int64 [G or 1], zeroed here.
+tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals,
+                       unsigned long long* per_vertex, cudaStream_t s);
+
+}  // namespace tc

@@ -1,0 +1,480 @@
+// tc_serve.cu -- continuous-batching request loop for count requests.
+//
+// No counterpart in the paper (it counts one graph per run); each request is
+// the paper's problem (Sec. 3) solved by the same build + count path.
+//
+// One request thread owns `slots` CUDA streams.  It admits queued requests in
+// arrival order whenever a slot is free and the HBM budget holds the resident
+// oriented CSRs plus every in-flight request's estimate; it retires a request
+// when the slot's completion event has fired.  Requests on different slots
+// overlap on the device.  Oriented CSRs built for a non-zero graph_key stay
+// resident (LRU eviction under the budget) so a repeated key skips the build.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tc_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    uint64_t key = 0;
+    int64_t n = 0, nnz = 0;
+    uint32_t flags = 0;
+    bool csr = true;
+    // pinned host copies of the inputs
+    int64_t* h_rp = nullptr;
+    int32_t* h_a = nullptr;  // col, or src
+    int32_t* h_b = nullptr;  // dst (edge list)
+    int64_t est_bytes = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+    // results (pinned host)
+    int64_t* h_total = nullptr;
+    int64_t* h_pv = nullptr;
+    std::vector<int64_t> pv;
+    int64_t total = 0;
+    tc_status status = TC_PENDING;
+    bool cache_hit = false;
+    bool done = false;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    Request* req = nullptr;
+    tc_ocsr* o = nullptr;
+    bool o_cached = false;       // o belongs to the resident cache
+    unsigned long long* d_total = nullptr;
+    unsigned long long* d_pv = nullptr;
+    int64_t d_pv_cap = 0;
+};
+
+struct CacheEntry {
+    tc_ocsr* o = nullptr;
+    int64_t bytes = 0;
+    int in_use = 0;
+    std::list<uint64_t>::iterator lru_it;
+};
+
+int64_t estimate_bytes(int64_t n, int64_t nnz, const tc::Tuning& t) {
+    const int64_t m = nnz / 2;
+    const int64_t dmax = std::max<int64_t>(1, (int64_t)std::sqrt((double)(2 * m)) + 1);
+    const int64_t iw = std::min(n, m) + m / t.chunk + 2;
+    const int64_t ic = dmax * m / ((int64_t)t.table_cap * t.chunk) + m / t.table_cap + m / t.chunk + m / (t.warp_max + 1) + 6;
+    const int64_t ocsr = 16 * (n + 1) + 4 * (2 * m + n) + 16 * (iw + ic);
+    const int64_t input = 8 * (n + 1) + 4 * nnz;
+    const int64_t scratch = 8 * n + 64 * 1024 + 8 * (n + 1);  // deg, pc, scan tiles, outputs
+    return ocsr + input + scratch + (1 << 20);
+}
+
+}  // namespace
+
+struct tc_server {
+    tc_server_config cfg{};
+    tc_ctx* ctx = nullptr;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::unordered_map<uint64_t, Request*> reqs;
+    std::unordered_map<uint64_t, CacheEntry> cache;
+    std::list<uint64_t> lru;  // front = most recent
+    int64_t resident = 0, inflight = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    tc_server_stats stats{};
+    // pinned staging buffers, reused by size class
+    std::multimap<size_t, void*> pinned_free;
+    std::mutex pin_mu;
+
+    void* pin_alloc(size_t bytes) {
+        size_t cls = 4096;
+        while (cls < bytes) cls <<= 1;
+        {
+            std::lock_guard<std::mutex> g(pin_mu);
+            auto it = pinned_free.find(cls);
+            if (it != pinned_free.end()) {
+                void* p = it->second;
+                pinned_free.erase(it);
+                return p;
+            }
+        }
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, cls, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void pin_free(void* p, size_t bytes) {
+        if (!p) return;
+        size_t cls = 4096;
+        while (cls < bytes) cls <<= 1;
+        std::lock_guard<std::mutex> g(pin_mu);
+        pinned_free.emplace(cls, p);
+    }
+    void free_inputs(Request* r) {
+        if (r->csr) {
+            pin_free(r->h_rp, sizeof(int64_t) * (r->n + 1));
+            pin_free(r->h_a, sizeof(int32_t) * std::max<int64_t>(r->nnz, 1));
+        } else {
+            pin_free(r->h_a, sizeof(int32_t) * std::max<int64_t>(r->nnz, 1));
+            pin_free(r->h_b, sizeof(int32_t) * std::max<int64_t>(r->nnz, 1));
+        }
+        r->h_rp = nullptr;
+        r->h_a = r->h_b = nullptr;
+    }
+
+    void evict_until(int64_t need) {
+        // drop least-recently-used resident oriented CSRs not in use
+        auto it = lru.end();
+        while (resident + inflight + need > cfg.hbm_budget_bytes && it != lru.begin()) {
+            --it;
+            auto ce = cache.find(*it);
+            if (ce == cache.end() || ce->second.in_use) continue;
+            tc_ocsr_release(ce->second.o, slots[0].stream);  // stream-ordered; slot 0 is idle or ordered after
+            resident -= ce->second.bytes;
+            stats.evictions++;
+            cache.erase(ce);
+            it = lru.erase(it);
+        }
+    }
+
+    void finish(Request* r, tc_status st) {
+        r->status = st;
+        r->t_done = Clock::now();
+        r->done = true;
+        stats.finished++;
+    }
+
+    bool launch(Slot& sl, Request* r) {
+        cudaStream_t s = sl.stream;
+        tc_ctx* c = ctx;
+        tc_ocsr* o = nullptr;
+        bool hit = false;
+        if (r->key) {
+            auto ce = cache.find(r->key);
+            if (ce != cache.end()) {
+                o = ce->second.o;
+                ce->second.in_use++;
+                lru.erase(ce->second.lru_it);
+                lru.push_front(r->key);
+                ce->second.lru_it = lru.begin();
+                hit = true;
+            }
+        }
+        tc_status st = TC_OK;
+        if (!o) {
+            // slot 0's releases are stream-ordered on slot 0; order this slot after them
+            tc_graph g{};
+            g.n = r->n;
+            g.nnz = r->nnz;
+            g.flags = TC_IN_HOST | (r->flags & TC_VALIDATE);
+            if (r->csr) { g.row_ptr = r->h_rp; g.col = r->h_a; }
+            else { g.src = r->h_a; g.dst = r->h_b; }
+            st = tc_build_oriented_csr(c, &g, &o, s);
+        }
+        if (st == TC_OK) {
+            if (sl.d_pv_cap < r->n && cfg.per_vertex) {
+                if (sl.d_pv) cudaFreeAsync(sl.d_pv, s);
+                sl.d_pv = nullptr;
+                sl.d_pv_cap = 0;
+                if (cudaMallocAsync((void**)&sl.d_pv, sizeof(int64_t) * std::max<int64_t>(r->n, 1), s) == cudaSuccess)
+                    sl.d_pv_cap = r->n;
+                else st = TC_ERR_OOM;
+            }
+        }
+        if (st == TC_OK) st = tc::count_device(c, o, sl.d_total, cfg.per_vertex ? sl.d_pv : nullptr, s);
+        if (st == TC_OK) {
+            cudaMemcpyAsync(r->h_total, sl.d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (cfg.per_vertex && r->n > 0)
+                cudaMemcpyAsync(r->h_pv, sl.d_pv, sizeof(int64_t) * r->n, cudaMemcpyDeviceToHost, s);
+            cudaEventRecord(sl.ev, s);
+        }
+        if (st != TC_OK) {
+            if (o && !hit) tc_ocsr_release(o, s);
+            if (hit) cache[r->key].in_use--;
+            inflight -= r->est_bytes;
+            free_inputs(r);
+            finish(r, st);
+            return false;
+        }
+        sl.req = r;
+        sl.o = o;
+        sl.o_cached = hit;
+        r->cache_hit = hit;
+        if (hit) stats.cache_hits++;
+        return true;
+    }
+
+    void retire(Slot& sl) {
+        Request* r = sl.req;
+        r->total = *r->h_total;
+        if (cfg.per_vertex) r->pv.assign(r->h_pv, r->h_pv + r->n);
+        pin_free(r->h_total, sizeof(int64_t));
+        if (r->h_pv) pin_free(r->h_pv, sizeof(int64_t) * std::max<int64_t>(r->n, 1));
+        r->h_total = nullptr;
+        r->h_pv = nullptr;
+        free_inputs(r);
+        inflight -= r->est_bytes;
+        if (sl.o_cached) {
+            cache[r->key].in_use--;
+        } else if (r->key && !cache.count(r->key)) {
+            CacheEntry ce;
+            ce.o = sl.o;
+            tc_ocsr_view v;
+            tc_ocsr_get_view(sl.o, &v);
+            ce.bytes = v.bytes;
+            lru.push_front(r->key);
+            ce.lru_it = lru.begin();
+            cache[r->key] = ce;
+            resident += ce.bytes;
+        } else {
+            tc_ocsr_release(sl.o, sl.stream);
+        }
+        sl.req = nullptr;
+        sl.o = nullptr;
+        finish(r, TC_OK);
+    }
+
+    void loop() {
+        cudaSetDevice(cfg.device);
+        std::unique_lock<std::mutex> lk(mu);
+        while (true) {
+            bool progressed = false;
+            for (auto& sl : slots) {
+                if (sl.req && cudaEventQuery(sl.ev) == cudaSuccess) {
+                    retire(sl);
+                    progressed = true;
+                }
+            }
+            // admit in arrival order
+            while (!queue.empty()) {
+                Slot* free_slot = nullptr;
+                for (auto& sl : slots)
+                    if (!sl.req) { free_slot = &sl; break; }
+                if (!free_slot) break;
+                Request* r = queue.front();
+                const bool hit = r->key && cache.count(r->key);
+                const int64_t need = hit ? 0 : r->est_bytes;
+                if (resident + inflight + need > cfg.hbm_budget_bytes) evict_until(need);
+                if (resident + inflight + need > cfg.hbm_budget_bytes) {
+                    if (inflight == 0 && need > cfg.hbm_budget_bytes) {
+                        queue.pop_front();
+                        free_inputs(r);
+                        finish(r, TC_ERR_BUDGET);
+                        progressed = true;
+                        continue;
+                    }
+                    break;  // wait for in-flight work to retire
+                }
+                queue.pop_front();
+                r->est_bytes = need;
+                r->t_admit = Clock::now();
+                inflight += need;
+                stats.admitted++;
+                stats.peak_inflight_bytes = std::max(stats.peak_inflight_bytes, inflight);
+                launch(*free_slot, r);
+                int busy = 0;
+                for (auto& sl : slots) busy += sl.req != nullptr;
+                stats.peak_inflight = std::max(stats.peak_inflight, busy);
+                progressed = true;
+            }
+            stats.resident_bytes = resident;
+            if (progressed) cv_done.notify_all();
+            bool any_busy = false;
+            for (auto& sl : slots) any_busy |= sl.req != nullptr;
+            if (stop && queue.empty() && !any_busy) break;
+            if (!progressed) {
+                if (any_busy) cv_work.wait_for(lk, std::chrono::microseconds(20));
+                else cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            }
+        }
+    }
+};
+
+extern "C" {
+
+tc_status tc_server_create(const tc_server_config* cfg, const tc_config* tuning, tc_server** out) {
+    if (!out) return TC_ERR_INVALID_ARG;
+    *out = nullptr;
+    tc_server* s = new tc_server();
+    if (cfg) s->cfg = *cfg;
+    if (s->cfg.slots <= 0) s->cfg.slots = 8;
+    if (s->cfg.slots > 64) s->cfg.slots = 64;
+    if (s->cfg.hbm_budget_bytes <= 0) s->cfg.hbm_budget_bytes = 40ll << 30;
+    tc_status st = tc_ctx_create(s->cfg.device, tuning, &s->ctx);
+    if (st != TC_OK) {
+        delete s;
+        return st;
+    }
+    cudaSetDevice(s->cfg.device);
+    s->slots.resize(s->cfg.slots);
+    for (auto& sl : s->slots) {
+        cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+        cudaMalloc((void**)&sl.d_total, sizeof(int64_t));
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+        tc_server_destroy(s);
+        return TC_ERR_CUDA;
+    }
+    s->worker = std::thread([s] { s->loop(); });
+    *out = s;
+    return TC_OK;
+}
+
+void tc_server_destroy(tc_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->cfg.device);
+    cudaDeviceSynchronize();
+    for (auto& kv : s->cache) tc_ocsr_free(kv.second.o);
+    for (auto& sl : s->slots) {
+        if (sl.d_total) cudaFree(sl.d_total);
+        if (sl.d_pv) cudaFree(sl.d_pv);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    for (auto& kv : s->reqs) {
+        s->free_inputs(kv.second);
+        delete kv.second;
+    }
+    for (auto& kv : s->pinned_free) cudaFreeHost(kv.second);
+    if (s->ctx) tc_ctx_destroy(s->ctx);
+    delete s;
+}
+
+tc_status tc_submit(tc_server* s, const tc_graph* g, uint64_t graph_key, uint64_t* ticket) {
+    if (!s || !g || !ticket) return TC_ERR_INVALID_ARG;
+    if (g->n < 0 || g->n > 0x7fffffffLL || g->nnz < 0) return TC_ERR_INVALID_ARG;
+    Request* r = new Request();
+    r->key = graph_key;
+    r->n = g->n;
+    r->nnz = g->nnz;
+    r->flags = g->flags;
+    r->csr = g->row_ptr != nullptr;
+    r->t_submit = Clock::now();
+    bool ok = true;
+    if (r->csr) {
+        if (g->nnz > 0 && !g->col) ok = false;
+        r->h_rp = (int64_t*)s->pin_alloc(sizeof(int64_t) * (g->n + 1));
+        r->h_a = (int32_t*)s->pin_alloc(sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
+        ok = ok && r->h_rp && r->h_a;
+        if (ok) {
+            std::memcpy(r->h_rp, g->row_ptr, sizeof(int64_t) * (g->n + 1));
+            if (g->nnz) std::memcpy(r->h_a, g->col, sizeof(int32_t) * g->nnz);
+        }
+    } else {
+        if (g->nnz > 0 && (!g->src || !g->dst)) ok = false;
+        r->h_a = (int32_t*)s->pin_alloc(sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
+        r->h_b = (int32_t*)s->pin_alloc(sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
+        ok = ok && r->h_a && r->h_b;
+        if (ok && g->nnz) {
+            std::memcpy(r->h_a, g->src, sizeof(int32_t) * g->nnz);
+            std::memcpy(r->h_b, g->dst, sizeof(int32_t) * g->nnz);
+        }
+    }
+    r->h_total = (int64_t*)s->pin_alloc(sizeof(int64_t));
+    if (s->cfg.per_vertex) r->h_pv = (int64_t*)s->pin_alloc(sizeof(int64_t) * std::max<int64_t>(g->n, 1));
+    ok = ok && r->h_total && (!s->cfg.per_vertex || r->h_pv);
+    if (!ok) {
+        s->free_inputs(r);
+        if (r->h_total) s->pin_free(r->h_total, sizeof(int64_t));
+        if (r->h_pv) s->pin_free(r->h_pv, sizeof(int64_t) * std::max<int64_t>(g->n, 1));
+        delete r;
+        return TC_ERR_INVALID_ARG;
+    }
+    // edge lists are estimated as CSRs of twice the pair count
+    r->est_bytes = estimate_bytes(r->n, r->csr ? r->nnz : 2 * r->nnz, s->ctx->tun) + (r->csr ? 0 : 24 * r->nnz);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r->ticket = s->next_ticket++;
+        s->reqs[r->ticket] = r;
+        s->queue.push_back(r);
+        s->stats.submitted++;
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_all();
+    return TC_OK;
+}
+
+static void fill_result(const Request* r, tc_result* out) {
+    out->status = r->status;
+    out->total = r->total;
+    out->n = r->n;
+    out->per_vertex = r->pv.empty() ? nullptr : r->pv.data();
+    out->submit_to_done_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    out->queue_ms = r->status == TC_ERR_BUDGET ? out->submit_to_done_ms
+                                               : std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
+    out->cache_hit = r->cache_hit ? 1 : 0;
+}
+
+tc_status tc_poll(tc_server* s, uint64_t ticket, tc_result* out) {
+    if (!s || !out) return TC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return TC_ERR_NOT_FOUND;
+    if (!it->second->done) {
+        out->status = TC_PENDING;
+        return TC_PENDING;
+    }
+    fill_result(it->second, out);
+    return it->second->status;
+}
+
+tc_status tc_wait(tc_server* s, uint64_t ticket, int64_t timeout_ms, tc_result* out) {
+    if (!s || !out) return TC_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return TC_ERR_NOT_FOUND;
+    Request* r = it->second;
+    const auto deadline = Clock::now() + std::chrono::milliseconds(std::max<int64_t>(timeout_ms, 0));
+    while (!r->done) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !r->done) {
+            out->status = TC_ERR_TIMEOUT;
+            return TC_ERR_TIMEOUT;
+        }
+    }
+    fill_result(r, out);
+    return r->status;
+}
+
+tc_status tc_release(tc_server* s, uint64_t ticket) {
+    if (!s) return TC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return TC_ERR_NOT_FOUND;
+    if (!it->second->done) return TC_PENDING;
+    delete it->second;
+    s->reqs.erase(it);
+    return TC_OK;
+}
+
+tc_status tc_server_get_stats(const tc_server* s, tc_server_stats* out) {
+    if (!s || !out) return TC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(const_cast<tc_server*>(s)->mu);
+    *out = s->stats;
+    out->resident_bytes = s->resident;
+    return TC_OK;
+}
+
+}  // extern "C"

@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 from dataclasses import dataclass
 
 import numpy as np
@@ -32,12 +33,19 @@ _i64, _i32, _u64, _f64, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, cty
 def build(force: bool = False) -> str:
     """Compile ``libtcgen.so`` in place with gcc (OpenMP, portable flags)."""
     src = os.path.join(_HERE, "tcgen.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+    stamp = _SO + ".arch"
+    try:
+        arch_ok = open(stamp).read().strip() == platform.machine()
+    except OSError:
+        arch_ok = False
+    if force or not arch_ok or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         import subprocess
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
                                "-o", tmp, src, "-lm"])
         os.replace(tmp, _SO)
+        with open(stamp, "w") as f:
+            f.write(platform.machine() + "\n")
     return _SO
 
 
