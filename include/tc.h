@@ -83,12 +83,15 @@ typedef struct tc_config {
                               thread each (the paper's TwoSmall); default 8 */
     int32_t warp_max;      /* pivots with d+ <= warp_max probe a warp-private table; larger pivots a
                               CTA-wide table (the paper's TwoLarge role); default 64 */
-    int32_t table_cap;     /* keys per CTA table segment (power of two, <= 8192); longer lists are
-                              split into segments; default 2048 */
+    int32_t table_cap;     /* keys per CTA table segment (power of two, 16..4096); longer lists are
+                              split into segments; default 1024 */
     int32_t probe;         /* 0/1 = open-addressing hash probe, 2 = binary search of the sorted list */
-    int32_t cta_threads;   /* threads per CTA of the CTA-table kernel (128..1024); default 512 */
-    int32_t chunk;         /* partners per work item; default 256 */
-    int32_t reserved[10];
+    int32_t cta_threads;   /* threads per CTA of the CTA-table kernel (64..1024); default 256 */
+    int32_t chunk;         /* partners per work item; default 512 */
+    int32_t bitmap_bits;   /* CTA items whose pivot list spans at most this many rank ids (vertices
+                              renamed in (degree, id) order) probe a shared-memory bitmap instead of
+                              the hash table; multiple of 32, <= 262144; default 131072; -1 = never */
+    int32_t reserved[9];
 } tc_config;
 
 typedef struct tc_ctx tc_ctx;
@@ -101,7 +104,7 @@ typedef struct tc_ocsr tc_ocsr;
 enum {
     TC_PH_DEGREE = 0, TC_PH_VALIDATE, TC_PH_ORIENT_COUNT, TC_PH_ORIENT_SCAN, TC_PH_ORIENT_SCATTER,
     TC_PH_PIVOT_COUNT, TC_PH_PIVOT_SCAN, TC_PH_PIVOT_SCATTER, TC_PH_ITEMS, TC_PH_COUNT_SMALL,
-    TC_PH_COUNT_WARP, TC_PH_COUNT_CTA, TC_PH_EDGE_SORT, TC_PH_COUNT_INIT
+    TC_PH_COUNT_WARP, TC_PH_COUNT_CTA, TC_PH_EDGE_SORT, TC_PH_COUNT_INIT, TC_PH_RANK, TC_PH_RELABEL
 };
 typedef struct tc_trace {
     int64_t launches;                        /* kernel launches since the last read */

@@ -37,7 +37,7 @@ class tc_graph(C.Structure):
 class tc_config(C.Structure):
     _fields_ = [("small_max", C.c_int32), ("warp_max", C.c_int32), ("table_cap", C.c_int32),
                 ("probe", C.c_int32), ("cta_threads", C.c_int32), ("chunk", C.c_int32),
-                ("reserved", C.c_int32 * 10)]
+                ("bitmap_bits", C.c_int32), ("reserved", C.c_int32 * 9)]
 
 
 class tc_ocsr_view(C.Structure):
@@ -63,7 +63,7 @@ class tc_result(C.Structure):
 
 TRACE_PHASES = ("degree", "validate", "orient_count", "orient_scan", "orient_scatter", "pivot_count",
                 "pivot_scan", "pivot_scatter", "items", "count_small", "count_warp", "count_cta", "edge_sort",
-                "count_init")
+                "count_init", "rank", "relabel")
 
 
 class tc_trace(C.Structure):

@@ -1,6 +1,7 @@
 // tc_api.cu -- the C ABI (include/tc.h): contexts, oriented-CSR handles,
 // single-graph and batched counting, CUDA-graph batch plans.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -53,9 +54,22 @@ PhaseScope::~PhaseScope() {
     }
 }
 
+// Defaults, then TC_SMALL_MAX / TC_WARP_MAX / TC_TABLE_CAP / TC_PROBE /
+// TC_CTA_THREADS / TC_CHUNK from the environment, then non-zero fields of c.
 static void apply_config(Tuning& t, const tc_config* c) {
     Tuning d;
     t = d;
+    auto env = [](const char* name, int& field) {
+        const char* v = std::getenv(name);
+        if (v && *v) field = std::atoi(v);
+    };
+    env("TC_SMALL_MAX", t.small_max);
+    env("TC_WARP_MAX", t.warp_max);
+    env("TC_TABLE_CAP", t.table_cap);
+    env("TC_PROBE", t.probe);
+    env("TC_CTA_THREADS", t.cta_threads);
+    env("TC_CHUNK", t.chunk);
+    env("TC_BITMAP_BITS", t.bitmap_bits);
     if (!c) return;
     if (c->small_max > 0) t.small_max = c->small_max;
     if (c->small_max < 0) t.small_max = 0;  // negative disables the thread-per-edge class
@@ -64,14 +78,17 @@ static void apply_config(Tuning& t, const tc_config* c) {
     if (c->probe > 0) t.probe = c->probe;
     if (c->cta_threads > 0) t.cta_threads = c->cta_threads;
     if (c->chunk > 0) t.chunk = c->chunk;
+    if (c->bitmap_bits > 0) t.bitmap_bits = c->bitmap_bits;
+    if (c->bitmap_bits < 0) t.bitmap_bits = 0;
 }
 
 static bool config_ok(const Tuning& t) {
     auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
     return t.small_max >= 0 && t.small_max <= 64 && t.warp_max >= 2 && t.warp_max <= 1024 &&
-           pow2(t.table_cap) && t.table_cap >= 16 && t.table_cap <= 8192 && t.warp_max <= t.table_cap &&
+           pow2(t.table_cap) && t.table_cap >= 16 && t.table_cap <= 4096 && t.warp_max <= t.table_cap &&
            (t.probe == 1 || t.probe == 2) && t.cta_threads >= 64 && t.cta_threads <= 1024 &&
-           t.cta_threads % 32 == 0 && t.chunk >= 1 && t.chunk <= (1 << 20);
+           t.cta_threads % 32 == 0 && t.chunk >= 1 && t.chunk <= (1 << 20) && t.bitmap_bits >= 0 &&
+           t.bitmap_bits <= 262144 && t.bitmap_bits % 32 == 0;
 }
 
 static bool is_host_ptr(const void* p) {
@@ -124,7 +141,8 @@ static tc_status count_any(tc_ctx* ctx, const tc_ocsr* o, int64_t* totals, int64
 
 static void release_ocsr(tc_ocsr* o, cudaStream_t s, bool async) {
     if (!o) return;
-    void* ptrs[] = {o->rpp, o->colp, o->dplus, o->prp, o->pcol, o->items_warp, o->items_cta, o->dc, o->row_graph};
+    void* ptrs[] = {o->rpp,  o->colp, o->dplus,      o->rank,      o->perm, o->colr,
+                    o->prp, o->pcol, o->items_warp, o->items_cta, o->dc,   o->row_graph};
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(o->device);
@@ -229,6 +247,7 @@ tc_status tc_ctx_get_config(const tc_ctx* ctx, tc_config* out) {
     out->probe = ctx->tun.probe;
     out->cta_threads = ctx->tun.cta_threads;
     out->chunk = ctx->tun.chunk;
+    out->bitmap_bits = ctx->tun.bitmap_bits;
     return TC_OK;
 }
 
@@ -437,20 +456,26 @@ tc_status tc_batch_plan_create(tc_ctx* ctx, const tc_batch* b, int64_t* totals, 
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_err(ctx, e, "plan: eager pass");
     }
+    // capture on a private stream (the legacy default stream cannot be captured)
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "plan: capture stream");
     const bool trace_was = ctx->trace;
     ctx->trace = false;
-    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         ctx->trace = trace_was;
+        cudaStreamDestroy(cs);
         return cuda_err(ctx, e, "plan: begin capture");
     }
     tc_ocsr* o = nullptr;
-    st = build_from_device_csr(ctx, d.n, d.nnz, d.row_ptr, d.col, d.vtx_off, d.G, false, &o, s);
-    if (st == TC_OK) st = count_device(ctx, o, (unsigned long long*)totals, (unsigned long long*)per_vertex, s);
-    if (o) release_ocsr(o, s, true);
+    st = build_from_device_csr(ctx, d.n, d.nnz, d.row_ptr, d.col, d.vtx_off, d.G, false, &o, cs);
+    if (st == TC_OK) st = count_device(ctx, o, (unsigned long long*)totals, (unsigned long long*)per_vertex, cs);
+    if (o) release_ocsr(o, cs, true);
     cudaGraph_t graph = nullptr;
-    e = cudaStreamEndCapture(s, &graph);
+    e = cudaStreamEndCapture(cs, &graph);
     ctx->trace = trace_was;
+    cudaStreamDestroy(cs);
     if (st != TC_OK) {
         if (graph) cudaGraphDestroy(graph);
         return st;

@@ -14,6 +14,8 @@ namespace tc {
 // ============================================================================
 // Device-wide exclusive scan (reduce-then-scan over 2048-element tiles)
 // ============================================================================
+constexpr int kBigRow = 4096;     // rows longer than this are oriented chunk by chunk
+constexpr int kBigChunk = 8192;   // entries per chunk of a long row
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -129,6 +131,29 @@ __global__ void k_row_graph(int64_t G, const int64_t* __restrict__ vtx_off, int3
         for (int64_t v = vtx_off[g] + threadIdx.x; v < vtx_off[g + 1]; v += blockDim.x) row_graph[v] = (int32_t)g;
 }
 
+// rank(v) = position of v in (degree, id) order: sort keys deg << b | v
+__global__ void k_rank_keys(int64_t n, const int32_t* __restrict__ deg, int b, unsigned long long* __restrict__ keys) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        keys[v] = ((unsigned long long)deg[v] << b) | (unsigned long long)v;
+}
+
+__global__ void k_rank_from_sorted(int64_t n, const unsigned long long* __restrict__ sorted, int b,
+                                   int32_t* __restrict__ rank, int32_t* __restrict__ perm) {
+    const unsigned long long mask = (1ull << b) - 1ull;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)(sorted[r] & mask);
+        perm[r] = v;
+        rank[v] = (int32_t)r;
+    }
+}
+
+// colr[e] = rank[colp[e]]: the oriented lists renamed to rank ids
+__global__ void k_relabel(int64_t m, const int32_t* __restrict__ colp, const int32_t* __restrict__ rank,
+                          int32_t* __restrict__ colr) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        colr[e] = rank[colp[e]];
+}
+
 // ============================================================================
 // validation of a CSR input (TC_VALIDATE): ids in range, rows strictly
 // ascending (sorted, no duplicates), no self-loops, symmetric.
@@ -197,6 +222,10 @@ __global__ void __launch_bounds__(256) k_orient(int64_t n, const int64_t* __rest
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS; u < n; u += ngroups) {
         const int64_t b = rp[u], e = rp[u + 1];
         const int du = (int)(e - b);
+        if (du > kBigRow) {  // long rows are cut into chunks for k_orient_big
+            if (!SCATTER && sub == 0) cnt[u] = 0;
+            continue;
+        }
         const int64_t base = BATCH ? vtx_off[row_graph[u]] : 0;
         int kept = 0;
         int64_t out = 0;
@@ -213,6 +242,78 @@ __global__ void __launch_bounds__(256) k_orient(int64_t n, const int64_t* __rest
             kept += __popc(mine);
         }
         if (!SCATTER && sub == 0) cnt[u] = kept;
+    }
+}
+
+// Rows longer than kBigRow are cut into chunks of kBigChunk entries, each
+// handled by one CTA, so that hub rows do not serialise on one warp.  The
+// count pass sums each chunk's kept entries; the scatter pass places a
+// chunk's kept entries after those of the row's earlier chunks.
+struct BigChunk {
+    int u, j, first, pad;
+};
+
+__global__ void k_big_chunks(int64_t n, const int64_t* __restrict__ rp, BigChunk* __restrict__ chunks,
+                             int64_t cap, unsigned long long* __restrict__ n_chunks) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = rp[u + 1] - rp[u];
+        if (d <= kBigRow) continue;
+        const int nch = (int)((d + kBigChunk - 1) / kBigChunk);
+        const unsigned long long first = atomicAdd(n_chunks, (unsigned long long)nch);
+        for (int j = 0; j < nch; ++j)
+            if ((int64_t)(first + j) < cap) chunks[first + j] = BigChunk{(int)u, j, (int)first, 0};
+    }
+}
+
+template <bool SCATTER, bool BATCH>
+__global__ void __launch_bounds__(256) k_orient_big(const BigChunk* __restrict__ chunks,
+                                                    const unsigned long long* __restrict__ n_chunks, int64_t cap,
+                                                    const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                    const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
+                                                    const int64_t* __restrict__ vtx_off, int32_t* __restrict__ cnt,
+                                                    int32_t* __restrict__ chunk_cnt, const int64_t* __restrict__ rpp,
+                                                    int32_t* __restrict__ colp) {
+    __shared__ int s_w[8];
+    __shared__ long long s_off;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t nc = (int64_t)min(*n_chunks, (unsigned long long)cap);
+    for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+        const BigChunk ch = chunks[c];
+        const int64_t u = ch.u;
+        const int64_t rb = rp[u], re = rp[u + 1];
+        const int du = (int)(re - rb);
+        const int64_t b = rb + (int64_t)ch.j * kBigChunk, e = min(re, b + kBigChunk);
+        const int64_t base = BATCH ? vtx_off[row_graph[u]] : 0;
+        if (SCATTER && threadIdx.x == 0) {
+            long long off = rpp[u];
+            for (int64_t k = ch.first; k < c; ++k) off += chunk_cnt[k];
+            s_off = off;
+        }
+        int run = 0;
+        for (int64_t r0 = b; r0 < e; r0 += blockDim.x) {
+            const int64_t i = r0 + threadIdx.x;
+            const bool valid = i < e;
+            const int64_t v = valid ? (int64_t)col[i] + base : 0;
+            const int dv = valid ? deg[v] : 0;
+            const bool keep = valid && (du < dv || (du == dv && u < v));
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) s_w[w] = __popc(bal);
+            __syncthreads();
+            int before = 0, tot = 0;
+            for (int k = 0; k < nw; ++k) {
+                const int c2 = s_w[k];
+                if (k < w) before += c2;
+                tot += c2;
+            }
+            if (SCATTER && keep) colp[s_off + run + before + __popc(bal & ((1u << lane) - 1u))] = (int32_t)v;
+            run += tot;
+            __syncthreads();
+        }
+        if (!SCATTER && threadIdx.x == 0) {
+            chunk_cnt[c] = run;
+            if (run) atomicAdd(&cnt[u], run);
+        }
+        __syncthreads();
     }
 }
 
@@ -417,6 +518,9 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     A((void**)&o->rpp, sizeof(int64_t) * n1);
     A((void**)&o->colp, sizeof(int32_t) * std::max<int64_t>(m, 1));
     A((void**)&o->dplus, sizeof(int32_t) * std::max<int64_t>(n, 1));
+    A((void**)&o->rank, sizeof(int32_t) * std::max<int64_t>(n, 1));
+    A((void**)&o->perm, sizeof(int32_t) * std::max<int64_t>(n, 1));
+    A((void**)&o->colr, sizeof(int32_t) * std::max<int64_t>(m, 1));
     A((void**)&o->prp, sizeof(int64_t) * n1);
     A((void**)&o->pcol, sizeof(int32_t) * std::max<int64_t>(m, 1));
     A((void**)&o->items_warp, sizeof(Item) * o->items_warp_cap);
@@ -431,7 +535,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         dev_free(deg, s); dev_free(pc, s); dev_free(scan_tmp, s);
         return set_err(ctx, TC_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
-    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (2 * m + n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
+    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 3 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
                          + (batch ? sizeof(int32_t) * n : 0));
     cudaMemsetAsync(o->dc, 0, sizeof(DevCounters), s);
 
@@ -463,14 +567,55 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
             return set_err(ctx, TC_ERR_INVALID_GRAPH, "input is not a simple symmetric sorted CSR (code " + std::to_string(herr) + ")");
         }
     }
+    // rank order (degree, id): one stable radix sort of n keys
+    if (n > 0) {
+        PhaseScope ph(ctx, kPhRank, s);
+        int b = 1;
+        while (((int64_t)1 << b) < n) ++b;
+        unsigned long long *ka = nullptr, *kb = nullptr, *sorted = nullptr;
+        e = dev_alloc((void**)&ka, sizeof(unsigned long long) * n, s);
+        if (e == cudaSuccess) e = dev_alloc((void**)&kb, sizeof(unsigned long long) * n, s);
+        if (e == cudaSuccess) {
+            k_rank_keys<<<grid_for(n, 256, ns), 256, 0, s>>>(n, deg, b, ka);
+            radix_sort_u64(ka, kb, n, 2 * b, s, &sorted, &ctx->launches);
+            k_rank_from_sorted<<<grid_for(n, 256, ns), 256, 0, s>>>(n, sorted, b, o->rank, o->perm);
+            ctx->launches += 2;
+        }
+        dev_free(ka, s);
+        dev_free(kb, s);
+        if (e != cudaSuccess) {
+            dev_free(deg, s); dev_free(pc, s); dev_free(scan_tmp, s);
+            tc_ocsr_free(o);
+            return set_err(ctx, TC_ERR_OOM, "rank: device allocation failed");
+        }
+    }
     const int gs = pick_group(n, nnz);
     const unsigned og = grid_for(n * gs, 256, ns, 16);
+    // long rows: chunk list (bounded by nnz/kBigChunk + nnz/kBigRow)
+    const int64_t bc_cap = nnz / kBigChunk + nnz / kBigRow + 2;
+    BigChunk* bchunks = nullptr;
+    int32_t* bcnt = nullptr;
+    unsigned long long* nbc = nullptr;
+    e = dev_alloc((void**)&bchunks, sizeof(BigChunk) * bc_cap, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&bcnt, sizeof(int32_t) * bc_cap, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&nbc, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        dev_free(bchunks, s); dev_free(bcnt, s); dev_free(nbc, s);
+        dev_free(deg, s); dev_free(pc, s); dev_free(scan_tmp, s);
+        tc_ocsr_free(o);
+        return set_err(ctx, TC_ERR_OOM, "orient: device allocation failed");
+    }
+    const unsigned bg = (unsigned)std::max(1, ns * 4);
     // a-2: kept count per row = d+(u)
     {
         PhaseScope ph(ctx, kPhOrientCount, s);
+        cudaMemsetAsync(nbc, 0, sizeof(unsigned long long), s);
+        if (n > 0) k_big_chunks<<<grid_for(n, 256, ns), 256, 0, s>>>(n, row_ptr, bchunks, bc_cap, nbc);
         if (batch) launch_orient<false, true>(gs, og, s, n, row_ptr, col, deg, o->row_graph, vtx_off, o->dplus, nullptr, nullptr);
         else launch_orient<false, false>(gs, og, s, n, row_ptr, col, deg, nullptr, nullptr, o->dplus, nullptr, nullptr);
-        TC_LAUNCH(ctx);
+        if (batch) k_orient_big<false, true><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, o->row_graph, vtx_off, o->dplus, bcnt, nullptr, nullptr);
+        else k_orient_big<false, false><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, nullptr, nullptr, o->dplus, bcnt, nullptr, nullptr);
+        ctx->launches += 3;
     }
     // a-3: row offsets of the oriented CSR, then the stable scatter
     {
@@ -482,6 +627,16 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         PhaseScope ph(ctx, kPhOrientScatter, s);
         if (batch) launch_orient<true, true>(gs, og, s, n, row_ptr, col, deg, o->row_graph, vtx_off, nullptr, o->rpp, o->colp);
         else launch_orient<true, false>(gs, og, s, n, row_ptr, col, deg, nullptr, nullptr, nullptr, o->rpp, o->colp);
+        if (batch) k_orient_big<true, true><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, o->row_graph, vtx_off, nullptr, bcnt, o->rpp, o->colp);
+        else k_orient_big<true, false><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, nullptr, nullptr, nullptr, bcnt, o->rpp, o->colp);
+        ctx->launches += 2;
+    }
+    dev_free(bchunks, s);
+    dev_free(bcnt, s);
+    dev_free(nbc, s);
+    if (m > 0) {
+        PhaseScope ph(ctx, kPhRelabel, s);
+        k_relabel<<<grid_for(m, 256, ns, 16), 256, 0, s>>>(m, o->colp, o->rank, o->colr);
         TC_LAUNCH(ctx);
     }
     // a-4: classify, group oriented edges by pivot, cut work items

@@ -41,6 +41,10 @@ struct CountArgs {
     unsigned long long* totals;   // [G] (batch) or [1]
     unsigned long long* t;        // per-vertex counts or nullptr
     const int32_t* row_graph;     // batch: graph of each vertex, else nullptr
+    const int32_t* colr;          // oriented lists in rank ids
+    const int32_t* perm;          // rank id -> vertex id
+    int bitmap_bits;              // max span (rank ids) of a bitmap table; 0 = off
+    int u_ints;                   // ints of the table region of k_count_cta
     int64_t n;
     int cap;                      // keys per table segment
     int small_max;
@@ -102,68 +106,293 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 }
 
 // One warp intersects the partners pb+first, pb+first+stride, ... (in groups
-// of 32) with the table.  pcnt: this warp's 32 shared counters.
+// of 32, one partner per lane) with the table.
+//
+// The lists of the 32 partners are flattened into one sequence of
+// tot = sum d+(q) elements; window k0 .. k0+31 puts element k0+lane on lane
+// `lane`.  The owner of an element is found without a search: every partner
+// marks the position where its list starts (all partner lists are non-empty,
+// the partition guarantees it), the marks of a window are OR-reduced into a
+// bit mask M, and the owner of position lane is (partners started before the
+// window) + popc(M & lanes <= lane) - 1.  Each element is probed in the table;
+// a ballot of the hits lets every partner lane count the hits that fall in
+// its own range of the window, so per-partner counts need no atomics.
+constexpr int kUnroll = 4;
+
 template <bool PV, int PROBE>
-__device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, int* keys, int* cnts, int logS,
+__device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, const int* keys, int* cnts, int logS,
                                                             int len, int64_t pbase, int pb, int pe, int first,
-                                                            int stride, int* pcnt) {
+                                                            int stride) {
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const unsigned le_mask = lane == 31 ? FULL : ((2u << lane) - 1u);
     unsigned long long acc = 0;
     for (int g0 = pb + first; g0 < pe; g0 += stride) {
         const int i = g0 + lane;
         const bool valid = i < pe;
         const int q = valid ? a.pcol[pbase + i] : 0;
         const int64_t qb = valid ? a.rpp[q] : 0;
-        const int dq = valid ? a.dp[q] : 0;
+        const int dq = valid ? (int)(a.rpp[q + 1] - qb) : 0;
         const int incl = warp_incl_scan_i(dq);
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        const int tot = __shfl_sync(FULL, incl, 31);
         const int excl = incl - dq;
-        pcnt[lane] = 0;
-        __syncwarp();
-        for (int k0 = 0; k0 < tot; k0 += 32) {
-            const int k = k0 + lane;
-            // owner partner j of flattened element k: the last lane with excl_j <= k
-            int j = 0;
+        const int64_t base = qb - excl;  // element k of partner q sits at colp[base + k]
+        int myc = 0, P = 0;
+        for (int k0 = 0; k0 < tot; k0 += 32 * kUnroll) {
+            int w[kUnroll];
+            bool in[kUnroll];
 #pragma unroll
-            for (int s = 16; s; s >>= 1) {
-                const int ej = __shfl_sync(0xffffffffu, excl, j + s);
-                if (ej <= k) j += s;
+            for (int u = 0; u < kUnroll; ++u) {
+                const int s = excl - (k0 + 32 * u);
+                const unsigned bit = (valid && s >= 0 && s < 32) ? (1u << s) : 0u;
+                const unsigned M = __reduce_or_sync(FULL, bit);
+                const int j = P + __popc(M & le_mask) - 1;
+                P += __popc(M);
+                const int64_t bj = __shfl_sync(FULL, base, j & 31);
+                const int k = k0 + 32 * u + lane;
+                in[u] = k < tot;
+                w[u] = in[u] ? a.colp[bj + k] : 0;
             }
-            const int64_t qbj = __shfl_sync(0xffffffffu, qb, j);
-            const int ej = __shfl_sync(0xffffffffu, excl, j);
-            if (k < tot) {
-                const int w = a.colp[qbj + (k - ej)];
-                const int h = table_find<PROBE>(keys, logS, len, w);
-                if (h >= 0) {
-                    if (PV) atomicAdd(&cnts[h], 1);
-                    atomicAdd(&pcnt[j], 1);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                bool hit = false;
+                if (in[u]) {
+                    const int h = table_find<PROBE>(keys, logS, len, w[u]);
+                    if (h >= 0) {
+                        hit = true;
+                        if (PV) atomicAdd(&cnts[h], 1);
+                    }
+                }
+                const unsigned hm = __ballot_sync(FULL, hit);
+                if (hm) {
+                    const int s = excl - (k0 + 32 * u);
+                    const int lo = max(s, 0), hi = min(s + dq, 32);
+                    if (lo < hi) {
+                        const unsigned rm = (hi >= 32 ? FULL : ((1u << hi) - 1u)) & (FULL << lo);
+                        myc += __popc(hm & rm);
+                    }
                 }
             }
         }
-        __syncwarp();
-        const int c = pcnt[lane];
-        if (valid && c) {
-            acc += (unsigned long long)c;
-            if (PV) atomicAdd(&a.t[q], (unsigned long long)c);
+        if (valid && myc) {
+            acc += (unsigned long long)myc;
+            if (PV) atomicAdd(&a.t[q], (unsigned long long)myc);
         }
-        __syncwarp();
     }
     return acc;
 }
 
 // ---------------------------------------------------------------------------
 // CTA-table kernel (persistent; items from a global queue)
+//
+// The whole CTA shares one table.  The partners of an item are taken up to
+// blockDim at a time; their lists are flattened into one sequence of E
+// elements and every warp walks an equal contiguous range of it, 32 elements
+// per window, so the work is balanced whatever the partner lengths are.  The
+// owner of each element comes from the partners whose lists start inside the
+// window (an OR-reduced bit mask over the next 32 list starts), as in
+// warp_partners; per-partner hit counts are summed per run of equal owners.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_excl_scan_i(int v, int* sm, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int inc = warp_incl_scan_i(v);
+    if (lane == 31) sm[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int t = lane < nw ? sm[lane] : 0;
+        const int ti = warp_incl_scan_i(t);
+        if (lane < nw) sm[lane] = ti - t;
+        if (lane == 31) sm[32] = ti;
+    }
+    __syncthreads();
+    const int r = sm[w] + inc - v;
+    *total = sm[32];
+    __syncthreads();
+    return r;
+}
+
+struct CtaScratch {
+    int64_t* base;  // [blockDim]   list base of each partner, minus its flattened offset
+    int* ex;        // [blockDim+1] flattened offset of each partner's list (ex[NP] = E)
+    int* q;         // [blockDim]
+    int* cnt;       // [blockDim]   hits per partner
+    int* scan;      // [33]
+};
+
+// Table of one pivot segment.  Hash: open addressing over rank ids (or vertex
+// ids for the binary-search mode).  Bitmap: bit (x - lo) set for each key x,
+// with a per-word prefix of set bits so that a hit's counter index is its
+// ordinal among the keys.
+constexpr int kModeHash = 0;
+constexpr int kModeBitmap = 1;
+constexpr int kModeBsearch = 2;
+
+struct Table {
+    const int* keys;
+    int* cnts;
+    int logS, len;
+    const unsigned* bits;
+    const unsigned short* pre;
+    int lo, span;
+};
+
+// counter index of x (0 when !PV), or -1
+template <int MODE, bool PV>
+__device__ __forceinline__ int table_lookup(const Table& t, int x) {
+    if (MODE == kModeBitmap) {
+        const unsigned off = (unsigned)(x - t.lo);
+        if (off >= (unsigned)t.span) return -1;
+        const unsigned word = t.bits[off >> 5];
+        const unsigned b = off & 31u;
+        if (!((word >> b) & 1u)) return -1;
+        return PV ? (int)t.pre[off >> 5] + __popc(word & ((1u << b) - 1u)) : 0;
+    } else if (MODE == kModeHash) {
+        return table_find<kProbeHash>(t.keys, t.logS, t.len, x);
+    } else {
+        return table_find<kProbeBsearch>(t.keys, t.logS, t.len, x);
+    }
+}
+
+template <bool PV, int MODE>
+__device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, const int32_t* __restrict__ L,
+                                                           const Table& tb, int64_t pbase, int pb, int pe,
+                                                           const CtaScratch& sc) {
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const unsigned le_mask = lane == 31 ? FULL : ((2u << lane) - 1u);
+    unsigned long long acc = 0;
+    for (int c0 = pb; c0 < pe; c0 += blockDim.x) {
+        const int NP = min((int)blockDim.x, pe - c0);
+        int q = 0, dq = 0;
+        int64_t qb = 0;
+        if (tid < NP) {
+            q = a.pcol[pbase + c0 + tid];
+            qb = a.rpp[q];
+            dq = (int)(a.rpp[q + 1] - qb);
+        }
+        int E;
+        const int ex = block_excl_scan_i(dq, sc.scan, &E);
+        if (tid < NP) {
+            sc.ex[tid] = ex;
+            sc.base[tid] = qb - ex;
+            sc.q[tid] = q;
+            sc.cnt[tid] = 0;
+        }
+        if (tid == 0) sc.ex[NP] = E;
+        __syncthreads();
+        const int per = ((E + nw - 1) / nw + 31) & ~31;
+        const int r0 = warp * per, r1 = min(E, r0 + per);
+        if (r0 < r1) {
+            // owner of r0: the last partner whose list starts at or before r0
+            int lo = 0, hi = NP - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sc.ex[mid] <= r0) lo = mid; else hi = mid - 1;
+            }
+            int j0 = lo;
+            for (int k0 = r0; k0 < r1; k0 += 32 * kUnroll) {
+                int w[kUnroll], jj[kUnroll];
+                unsigned Ms[kUnroll];
+                bool in[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int kb = k0 + 32 * u;
+                    const int idx = j0 + 1 + lane;
+                    const int e_next = idx <= NP ? sc.ex[idx] : 0x7fffffff;
+                    const int sft = e_next - kb;
+                    const unsigned M = __reduce_or_sync(FULL, (sft >= 1 && sft < 32) ? (1u << sft) : 0u);
+                    const bool at32 = __any_sync(FULL, sft == 32);
+                    const int j = j0 + __popc(M & le_mask);
+                    const int k = kb + lane;
+                    in[u] = k < r1;
+                    jj[u] = j;
+                    Ms[u] = M;
+                    w[u] = in[u] ? L[sc.base[j] + k] : 0;
+                    j0 += __popc(M) + (at32 ? 1 : 0);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    bool hit = false;
+                    if (in[u]) {
+                        const int h = table_lookup<MODE, PV>(tb, w[u]);
+                        if (h >= 0) {
+                            hit = true;
+                            if (PV) atomicAdd(&tb.cnts[h], 1);
+                        }
+                    }
+                    const unsigned hm = __ballot_sync(FULL, hit);
+                    if (hm) {
+                        const unsigned M = Ms[u];
+                        if (lane == 0 || ((M >> lane) & 1u)) {  // head of a run of equal owners
+                            const unsigned above = M & ~le_mask;
+                            const int end = above ? __ffs(above) - 1 : 32;
+                            const unsigned rm = (end >= 32 ? FULL : ((1u << end) - 1u)) & (FULL << lane);
+                            const int c = __popc(hm & rm);
+                            if (c) atomicAdd(&sc.cnt[jj[u]], c);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < NP) {
+            const int c = sc.cnt[tid];
+            if (c) {
+                acc += (unsigned long long)c;
+                if (PV) atomicAdd(&a.t[sc.q[tid]], (unsigned long long)c);
+            }
+        }
+        __syncthreads();
+    }
+    return acc;
+}
+
+// ints of the table region: hash (keys + counts, 8*cap) or bitmap (words,
+// 16-bit word prefixes, counts), whichever is larger
+static int cta_table_ints(int cap, int bitmap_bits) {
+    const int words = bitmap_bits / 32;
+    const int bm = words + (words + 1) / 2 + cap;
+    return std::max(8 * cap, bm);
+}
+
+static size_t cta_smem_bytes(int u_ints, int threads) {
+    return (size_t)u_ints * sizeof(int) + (size_t)threads * sizeof(int64_t) + (size_t)(threads + 1) * sizeof(int) +
+           (size_t)2 * threads * sizeof(int) + 33 * sizeof(int) + 8;
+}
+
+__device__ __forceinline__ void block_minmax(int& mn, int& mx, int* red) {
+    for (int o = 16; o; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { red[w] = mn; red[32 + w] = mx; }
+    __syncthreads();
+    mn = 0x7fffffff;
+    mx = -1;
+    for (int i = 0; i < nw; ++i) { mn = min(mn, red[i]); mx = max(mx, red[32 + i]); }
+    __syncthreads();
+}
+
 template <bool PV, int PROBE>
 __global__ void __launch_bounds__(1024) k_count_cta(CountArgs a) {
-    extern __shared__ int smem[];
-    int* keys = smem;
-    int* cnts = smem + 2 * a.cap;
-    __shared__ int s_pcnt[32][32];
+    extern __shared__ __align__(16) int smem[];
+    int* U = smem;
+    CtaScratch sc;
+    sc.base = reinterpret_cast<int64_t*>(smem + ((a.u_ints + 1) & ~1));
+    sc.ex = reinterpret_cast<int*>(sc.base + blockDim.x);
+    sc.q = sc.ex + blockDim.x + 1;
+    sc.cnt = sc.q + blockDim.x;
+    sc.scan = sc.cnt + blockDim.x;
+    __shared__ int s_red[64];
     __shared__ unsigned s_item;
     __shared__ unsigned long long s_acc;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
+    // hash mode probes rank ids (so that a short span can use the bitmap);
+    // the binary-search mode probes the id-sorted lists
+    const int32_t* __restrict__ L = PROBE == kProbeHash ? a.colr : a.colp;
     const unsigned long long n_items = min(*a.n_items, a.items_cap);
+    const int wmax = a.bitmap_bits / 32;
     for (;;) {
         if (threadIdx.x == 0) {
             s_item = atomicAdd(a.queue, 1u);
@@ -176,34 +405,106 @@ __global__ void __launch_bounds__(1024) k_count_cta(CountArgs a) {
         const int p = item.p;
         const int64_t lb = a.rpp[p] + (int64_t)item.seg * a.cap;
         const int len = (int)min((int64_t)a.cap, a.rpp[p + 1] - lb);
-        int logS, S;
-        if (PROBE == kProbeHash) {
-            logS = max(5, 32 - __clz(2 * len - 1));
-            S = 1 << logS;
-            for (int i = threadIdx.x; i < S; i += blockDim.x) {
-                keys[i] = -1;
-                if (PV) cnts[i] = 0;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < len; i += blockDim.x) table_insert(keys, logS, a.colp[lb + i]);
-        } else {
-            logS = 0;
-            S = len;
+        Table tb{};
+        tb.len = len;
+        int mode = PROBE == kProbeHash ? kModeHash : kModeBsearch;
+        if (PROBE == kProbeHash && a.bitmap_bits > 0) {
+            int mn = 0x7fffffff, mx = -1;
             for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                keys[i] = a.colp[lb + i];
-                if (PV) cnts[i] = 0;
+                const int x = L[lb + i];
+                mn = min(mn, x);
+                mx = max(mx, x);
+            }
+            block_minmax(mn, mx, s_red);
+            if (mx - mn < a.bitmap_bits) {
+                mode = kModeBitmap;
+                tb.lo = mn;
+                tb.span = mx - mn + 1;
             }
         }
+        int nflush = 0;
+        if (mode == kModeBitmap) {
+            const int W = (tb.span + 31) >> 5;
+            unsigned* bits = reinterpret_cast<unsigned*>(U);
+            unsigned short* pre = reinterpret_cast<unsigned short*>(U + wmax);
+            tb.bits = bits;
+            tb.pre = pre;
+            tb.cnts = U + wmax + (wmax + 1) / 2;
+            for (int i = threadIdx.x; i < W; i += blockDim.x) bits[i] = 0u;
+            if (PV)
+                for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cnts[i] = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const unsigned off = (unsigned)(L[lb + i] - tb.lo);
+                atomicOr(&bits[off >> 5], 1u << (off & 31u));
+            }
+            __syncthreads();
+            if (PV) {  // prefix of set bits per word
+                const int per = (W + blockDim.x - 1) / blockDim.x;
+                const int w0 = threadIdx.x * per, w1 = min(W, w0 + per);
+                int c = 0;
+                for (int i = w0; i < w1; ++i) c += __popc(bits[i]);
+                int tot;
+                int run = block_excl_scan_i(c, sc.scan, &tot);
+                for (int i = w0; i < w1; ++i) {
+                    pre[i] = (unsigned short)run;
+                    run += __popc(bits[i]);
+                }
+            }
+            nflush = W;
+        } else if (mode == kModeHash) {
+            int* keys = U;
+            tb.keys = keys;
+            tb.cnts = U + 4 * a.cap;
+            tb.logS = max(5, 32 - __clz(4 * len - 1));  // load factor <= 1/4
+            const int S = 1 << tb.logS;
+            for (int i = threadIdx.x; i < S; i += blockDim.x) {
+                keys[i] = -1;
+                if (PV) tb.cnts[i] = 0;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < len; i += blockDim.x) table_insert(keys, tb.logS, L[lb + i]);
+            nflush = S;
+        } else {
+            int* keys = U;
+            tb.keys = keys;
+            tb.cnts = U + 4 * a.cap;
+            tb.logS = 0;
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                keys[i] = L[lb + i];
+                if (PV) tb.cnts[i] = 0;
+            }
+            nflush = len;
+        }
         __syncthreads();
-        unsigned long long acc = warp_partners<PV, PROBE>(a, keys, cnts, logS, len, a.prp[p], item.pb, item.pe,
-                                                          warp * 32, nw * 32, s_pcnt[warp]);
+        unsigned long long acc;
+        if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, sc);
+        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, sc);
+        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, sc);
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
         if (PV) {
-            for (int i = threadIdx.x; i < S; i += blockDim.x) {
-                const int c = cnts[i];
-                if (c) atomicAdd(&a.t[keys[i]], (unsigned long long)c);
+            if (mode == kModeBitmap) {
+                for (int i = threadIdx.x; i < nflush; i += blockDim.x) {
+                    unsigned b = tb.bits[i];
+                    int ord = tb.pre[i];
+                    while (b) {
+                        const int bit = __ffs(b) - 1;
+                        const int c = tb.cnts[ord];
+                        if (c) atomicAdd(&a.t[a.perm[tb.lo + i * 32 + bit]], (unsigned long long)c);
+                        b &= b - 1u;
+                        ++ord;
+                    }
+                }
+            } else {
+                for (int i = threadIdx.x; i < nflush; i += blockDim.x) {
+                    const int c = tb.cnts[i];
+                    if (c) {
+                        const int x = tb.keys[i];
+                        atomicAdd(&a.t[PROBE == kProbeHash ? a.perm[x] : x], (unsigned long long)c);
+                    }
+                }
             }
         }
         if (threadIdx.x == 0 && s_acc) {
@@ -222,10 +523,9 @@ template <bool PV, int PROBE>
 __global__ void __launch_bounds__(256) k_count_warp(CountArgs a, int wcap) {
     extern __shared__ int smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per_warp = 4 * wcap + 32;
+    const int per_warp = 8 * wcap;
     int* keys = smem + warp * per_warp;
-    int* cnts = keys + 2 * wcap;
-    int* pcnt = cnts + 2 * wcap;
+    int* cnts = keys + 4 * wcap;
     const unsigned long long n_items = min(*a.n_items, a.items_cap);
     for (;;) {
         unsigned it = 0;
@@ -238,7 +538,7 @@ __global__ void __launch_bounds__(256) k_count_warp(CountArgs a, int wcap) {
         const int len = (int)(a.rpp[p + 1] - lb);
         int logS, S;
         if (PROBE == kProbeHash) {
-            logS = max(5, 32 - __clz(2 * len - 1));
+            logS = max(5, 32 - __clz(4 * len - 1));  // load factor <= 1/4
             S = 1 << logS;
             for (int i = lane; i < S; i += 32) {
                 keys[i] = -1;
@@ -256,7 +556,7 @@ __global__ void __launch_bounds__(256) k_count_warp(CountArgs a, int wcap) {
         }
         __syncwarp();
         unsigned long long acc =
-            warp_partners<PV, PROBE>(a, keys, cnts, logS, len, a.prp[p], item.pb, item.pe, 0, 32, pcnt);
+            warp_partners<PV, PROBE>(a, keys, cnts, logS, len, a.prp[p], item.pb, item.pe, 0, 32);
         __syncwarp();
         if (PV) {
             for (int i = lane; i < S; i += 32) {
@@ -347,12 +647,14 @@ static cudaError_t launch_tables(tc_ctx* ctx, const CountArgs& base, const tc_oc
         a.items_cap = (unsigned long long)o->items_warp_cap;
         a.queue = queues + 0;
         const int wcap = std::max(16, pow2ceil(tun.warp_max));
-        const size_t smem = (size_t)8 * (4 * wcap + 32) * sizeof(int);
+        // 32*wcap bytes of table per warp; up to 8 warps per CTA within 192 KB
+        const int wpb = std::max(1, std::min(8, (192 * 1024) / (32 * wcap)));
+        const size_t smem = (size_t)wpb * (8 * wcap) * sizeof(int);
         auto kern = k_count_warp<PV, PROBE>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
-        kern<<<(unsigned)(num_sms * std::max(per_sm, 1)), 256, smem, s>>>(a, wcap);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem);
+        kern<<<(unsigned)(num_sms * std::max(per_sm, 1)), 32 * wpb, smem, s>>>(a, wcap);
     }
     // CTA-table items
     {
@@ -363,7 +665,8 @@ static cudaError_t launch_tables(tc_ctx* ctx, const CountArgs& base, const tc_oc
         a.n_items = &o->dc->n_items_cta;
         a.items_cap = (unsigned long long)o->items_cta_cap;
         a.queue = queues + 1;
-        const size_t smem = (size_t)4 * a.cap * sizeof(int);
+        a.u_ints = cta_table_ints(a.cap, a.bitmap_bits);
+        const size_t smem = cta_smem_bytes(a.u_ints, tun.cta_threads);
         auto kern = k_count_cta<PV, PROBE>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
@@ -403,6 +706,9 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.n = o->n;
     a.cap = tun.table_cap;
     a.small_max = tun.small_max;
+    a.colr = o->colr;
+    a.perm = o->perm;
+    a.bitmap_bits = tun.bitmap_bits;
     const int ns = ctx->num_sms;
 
     if (tun.small_max >= 2) {

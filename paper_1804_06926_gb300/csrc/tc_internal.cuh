@@ -33,10 +33,11 @@ struct __align__(16) Item {
 struct Tuning {
     int small_max = 8;
     int warp_max = 64;
-    int table_cap = 2048;
+    int table_cap = 1024;
     int probe = 1;          // 1 hash, 2 binary search
-    int cta_threads = 512;
-    int chunk = 256;
+    int cta_threads = 256;
+    int chunk = 512;
+    int bitmap_bits = 131072;  // CTA items whose list spans <= this many rank ids use a bitmap
 };
 
 }  // namespace tc
@@ -48,6 +49,9 @@ struct tc_ocsr {
     int64_t* rpp = nullptr;     // [n+1] oriented row offsets
     int32_t* colp = nullptr;    // [m]
     int32_t* dplus = nullptr;   // [n] out-degrees
+    int32_t* rank = nullptr;    // [n] position of each vertex in (degree, id) order
+    int32_t* perm = nullptr;    // [n] inverse of rank
+    int32_t* colr = nullptr;    // [m] colp relabelled to rank ids (same row layout)
     int64_t* prp = nullptr;     // [n+1] partner row offsets
     int32_t* pcol = nullptr;    // [m] partners (only the first n_pivot_edges used)
     tc::Item* items_warp = nullptr;
@@ -79,7 +83,8 @@ namespace tc {
 // Phase ids of the trace (tc_trace.phase_ms index).
 enum Phase {
     kPhDegree = 0, kPhValidate, kPhOrientCount, kPhOrientScan, kPhOrientScatter, kPhPivotCount, kPhPivotScan,
-    kPhPivotScatter, kPhItems, kPhCountSmall, kPhCountWarp, kPhCountCta, kPhEdgeSort, kPhCountInit, kNumPhases
+    kPhPivotScatter, kPhItems, kPhCountSmall, kPhCountWarp, kPhCountCta, kPhEdgeSort, kPhCountInit, kPhRank,
+    kPhRelabel, kNumPhases
 };
 
 // RAII phase marker: records an event pair on `s` when tracing is on.
@@ -111,6 +116,10 @@ size_t scan_tmp_bytes(int64_t n);
 tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr,
                                 const int32_t* col, const int64_t* vtx_off, int64_t G,
                                 bool validate, tc_ocsr** out, cudaStream_t s);
+
+// Stable LSD radix sort of uint64 keys on their low key_bits bits.
+cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64_t K, int key_bits, cudaStream_t s,
+                           unsigned long long** sorted, long long* launches);
 
 // Canonicalise a device edge list into a device CSR (library-owned buffers).
 tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t npairs, const int32_t* src, const int32_t* dst,

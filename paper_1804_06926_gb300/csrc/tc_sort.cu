@@ -93,6 +93,39 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long l
     }
 }
 
+// LSD radix sort of K keys on their low key_bits bits (8 bits per pass,
+// stable).  ka holds the input, kb is scratch of the same size; *sorted
+// receives whichever of the two holds the result.
+cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64_t K, int key_bits, cudaStream_t s,
+                           unsigned long long** sorted, long long* launches) {
+    *sorted = ka;
+    if (K <= 0) return cudaSuccess;
+    const int64_t ntiles = (K + kRsTile - 1) / kRsTile;
+    const int64_t nh = 256 * ntiles;
+    int32_t* hist = nullptr;
+    int64_t* hoff = nullptr;
+    void* stmp = nullptr;
+    const size_t stb = scan_tmp_bytes(nh);
+    cudaError_t e = dev_alloc((void**)&hist, sizeof(int32_t) * nh, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&hoff, sizeof(int64_t) * (nh + 1), s);
+    if (e == cudaSuccess) e = dev_alloc(&stmp, stb, s);
+    if (e == cudaSuccess) {
+        for (int shift = 0; shift < key_bits; shift += 8) {
+            k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, K, shift, hist, ntiles);
+            scan_i32_to_i64(hist, hoff, nh, stmp, stb, s);
+            k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, kb, K, shift, hoff, ntiles);
+            std::swap(ka, kb);
+            if (launches) *launches += 5;
+        }
+        *sorted = ka;
+        e = cudaGetLastError();
+    }
+    dev_free(hist, s);
+    dev_free(hoff, s);
+    dev_free(stmp, s);
+    return e;
+}
+
 // flag[i] = 1 for the first copy of a non-sentinel key
 __global__ void k_mark_unique(const unsigned long long* __restrict__ keys, int64_t K, unsigned long long sentinel,
                               int32_t* __restrict__ flag) {
@@ -180,14 +213,13 @@ tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t np, const int32_t* src, c
     int herr = 0;
     {
     PhaseScope ph(ctx, kPhEdgeSort, s);
-    ctx->launches += 8 + 5 * ((key_bits + 7) / 8);
+    ctx->launches += 8 + 5 * ((key_bits + 7) / 8);  // includes the radix-sort passes
     cudaMemsetAsync(err, 0, sizeof(int), s);
     if (np > 0) k_make_keys<<<grid, 256, 0, s>>>(np, src, dst, n, b, sentinel, ka, err);
-    for (int shift = 0; shift < key_bits && K > 0; shift += 8) {
-        k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, K, shift, hist, ntiles);
-        scan_i32_to_i64(hist, hoff, nh, stmp, stb, s);
-        k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, kb, K, shift, hoff, ntiles);
-        std::swap(ka, kb);
+    {
+        unsigned long long* sorted = ka;
+        radix_sort_u64(ka, kb, K, key_bits, s, &sorted, nullptr);
+        if (sorted != ka) std::swap(ka, kb);
     }
     if (K > 0) k_mark_unique<<<grid, 256, 0, s>>>(ka, K, sentinel, flag);
     scan_i32_to_i64(flag, pos, K, stmp, stb, s);

@@ -119,7 +119,10 @@ CONFIGS = [
     dict(probe=2),
     dict(probe=2, table_cap=32, warp_max=8, chunk=3),
     dict(cta_threads=128, chunk=7),
-    dict(cta_threads=1024, table_cap=8192, warp_max=1024),
+    dict(cta_threads=1024, table_cap=4096, warp_max=1024),
+    dict(bitmap_bits=-1),
+    dict(bitmap_bits=64, warp_max=4),
+    dict(bitmap_bits=262144, table_cap=64, warp_max=8, chunk=5),
 ]
 
 
