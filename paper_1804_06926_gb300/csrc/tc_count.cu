@@ -211,12 +211,19 @@ __device__ __forceinline__ int block_excl_scan_i(int v, int* sm, int* total) {
     return r;
 }
 
+// Per-CTA partner scratch: the partners of one sub-chunk, sorted by list
+// length class (longest first), and the warp tasks cut from them.
+constexpr int kClasses = 16;
 struct CtaScratch {
-    int64_t* base;  // [blockDim]   list base of each partner, minus its flattened offset
-    int* ex;        // [blockDim+1] flattened offset of each partner's list (ex[NP] = E)
-    int* q;         // [blockDim]
-    int* cnt;       // [blockDim]   hits per partner
-    int* scan;      // [33]
+    int64_t* qb;            // [pmax] list start of each sorted partner
+    int* q;                 // [pmax]
+    int* dq;                // [pmax]
+    unsigned char* tcls;    // [pmax] class of each task
+    int* ccnt;              // [kClasses] partners per class
+    int* coff;              // [kClasses] first sorted position of each class
+    int* toff;              // [kClasses] first task of each class
+    int* misc;              // [4]: task counter, number of tasks
+    int* scan;              // [33]
 };
 
 // Table of one pivot segment.  Hash: open addressing over rank ids (or vertex
@@ -253,93 +260,117 @@ __device__ __forceinline__ int table_lookup(const Table& t, int x) {
     }
 }
 
+// Lanes per partner for a list-length class c (lists of 2^c .. 2^(c+1)-1
+// elements): one lane up to 7 elements, then doubling up to a full warp, so
+// that every lane of a task walks about 4 to 8 elements per list.
+__device__ __forceinline__ int class_lanes(int c) { return 1 << min(max(c - 2, 0), 5); }
+
+// Intersect the item's partners [pb, pe) with the table.  Partners are taken
+// pmax at a time, counting-sorted by length class, and cut into warp tasks of
+// 32/G partners of one class with G lanes per partner (the dynamic grouping by
+// list size of Sec. 4.2.2, inside one CTA).  Warps take tasks longest class
+// first from a shared counter.  Every lane walks elements r, r+G, ... of its
+// partner's list, so loads are contiguous per partner and hits of a partner
+// stay in registers until a G-lane reduction.
 template <bool PV, int MODE>
 __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, const int32_t* __restrict__ L,
-                                                           const Table& tb, int64_t pbase, int pb, int pe,
+                                                           const Table& tb, int64_t pbase, int pb, int pe, int pmax,
                                                            const CtaScratch& sc) {
     const unsigned FULL = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const unsigned le_mask = lane == 31 ? FULL : ((2u << lane) - 1u);
+    const int tid = threadIdx.x, lane = tid & 31;
     unsigned long long acc = 0;
-    for (int c0 = pb; c0 < pe; c0 += blockDim.x) {
-        const int NP = min((int)blockDim.x, pe - c0);
-        int q = 0, dq = 0;
-        int64_t qb = 0;
-        if (tid < NP) {
-            q = a.pcol[pbase + c0 + tid];
-            qb = a.rpp[q];
-            dq = (int)(a.rpp[q + 1] - qb);
-        }
-        int E;
-        const int ex = block_excl_scan_i(dq, sc.scan, &E);
-        if (tid < NP) {
-            sc.ex[tid] = ex;
-            sc.base[tid] = qb - ex;
-            sc.q[tid] = q;
-            sc.cnt[tid] = 0;
-        }
-        if (tid == 0) sc.ex[NP] = E;
+    constexpr int kPer = 2;  // partners per thread while sorting (pmax <= 2 * blockDim)
+    for (int c0 = pb; c0 < pe; c0 += pmax) {
+        const int NP = min(pmax, pe - c0);
+        if (tid < kClasses) sc.ccnt[tid] = 0;
+        if (tid == 0) sc.misc[0] = 0;
         __syncthreads();
-        const int per = ((E + nw - 1) / nw + 31) & ~31;
-        const int r0 = warp * per, r1 = min(E, r0 + per);
-        if (r0 < r1) {
-            // owner of r0: the last partner whose list starts at or before r0
-            int lo = 0, hi = NP - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sc.ex[mid] <= r0) lo = mid; else hi = mid - 1;
-            }
-            int j0 = lo;
-            for (int k0 = r0; k0 < r1; k0 += 32 * kUnroll) {
-                int w[kUnroll], jj[kUnroll];
-                unsigned Ms[kUnroll];
-                bool in[kUnroll];
+        int rq[kPer], rd[kPer], rc[kPer], rs[kPer];
+        int64_t rb[kPer];
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int kb = k0 + 32 * u;
-                    const int idx = j0 + 1 + lane;
-                    const int e_next = idx <= NP ? sc.ex[idx] : 0x7fffffff;
-                    const int sft = e_next - kb;
-                    const unsigned M = __reduce_or_sync(FULL, (sft >= 1 && sft < 32) ? (1u << sft) : 0u);
-                    const bool at32 = __any_sync(FULL, sft == 32);
-                    const int j = j0 + __popc(M & le_mask);
-                    const int k = kb + lane;
-                    in[u] = k < r1;
-                    jj[u] = j;
-                    Ms[u] = M;
-                    w[u] = in[u] ? L[sc.base[j] + k] : 0;
-                    j0 += __popc(M) + (at32 ? 1 : 0);
-                }
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    bool hit = false;
-                    if (in[u]) {
-                        const int h = table_lookup<MODE, PV>(tb, w[u]);
-                        if (h >= 0) {
-                            hit = true;
-                            if (PV) atomicAdd(&tb.cnts[h], 1);
-                        }
-                    }
-                    const unsigned hm = __ballot_sync(FULL, hit);
-                    if (hm) {
-                        const unsigned M = Ms[u];
-                        if (lane == 0 || ((M >> lane) & 1u)) {  // head of a run of equal owners
-                            const unsigned above = M & ~le_mask;
-                            const int end = above ? __ffs(above) - 1 : 32;
-                            const unsigned rm = (end >= 32 ? FULL : ((1u << end) - 1u)) & (FULL << lane);
-                            const int c = __popc(hm & rm);
-                            if (c) atomicAdd(&sc.cnt[jj[u]], c);
-                        }
-                    }
-                }
+        for (int k = 0; k < kPer; ++k) {
+            const int i = tid + k * blockDim.x;
+            rc[k] = -1;
+            rq[k] = rd[k] = rs[k] = 0;
+            rb[k] = 0;
+            if (i < NP) {
+                rq[k] = a.pcol[pbase + c0 + i];
+                rb[k] = a.rpp[rq[k]];
+                rd[k] = (int)(a.rpp[rq[k] + 1] - rb[k]);
+                rc[k] = min(kClasses - 1, 31 - __clz(rd[k]));
+                rs[k] = atomicAdd(&sc.ccnt[rc[k]], 1);
             }
         }
         __syncthreads();
-        if (tid < NP) {
-            const int c = sc.cnt[tid];
-            if (c) {
-                acc += (unsigned long long)c;
-                if (PV) atomicAdd(&a.t[sc.q[tid]], (unsigned long long)c);
+        if (tid == 0) {
+            int pos = 0, task = 0;
+            for (int c = kClasses - 1; c >= 0; --c) {
+                sc.coff[c] = pos;
+                sc.toff[c] = task;
+                const int ppt = 32 / class_lanes(c);
+                pos += sc.ccnt[c];
+                task += (sc.ccnt[c] + ppt - 1) / ppt;
+            }
+            sc.misc[1] = task;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (rc[k] >= 0) {
+                const int pos = sc.coff[rc[k]] + rs[k];
+                sc.q[pos] = rq[k];
+                sc.qb[pos] = rb[k];
+                sc.dq[pos] = rd[k];
+            }
+        }
+        const int NT = sc.misc[1];
+        for (int t = tid; t < NT; t += blockDim.x) {
+            int c = kClasses - 1;
+            while (c > 0 && sc.toff[c - 1] <= t) --c;  // task ranges grow as the class falls
+            sc.tcls[t] = (unsigned char)c;
+        }
+        __syncthreads();
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&sc.misc[0], 1);
+            t = __shfl_sync(FULL, t, 0);
+            if (t >= NT) break;
+            const int c = sc.tcls[t];
+            const int G = class_lanes(c);
+            const int ppt = 32 / G;
+            const int sub = lane / G, r = lane % G;
+            const int i = sc.coff[c] + (t - sc.toff[c]) * ppt + sub;
+            const bool valid = i < sc.coff[c] + sc.ccnt[c];
+            const int dq = valid ? sc.dq[i] : 0;
+            const int64_t qb = valid ? sc.qb[i] : 0;
+            const int32_t* __restrict__ lp = L + qb;
+            int myc = 0;
+            int k = r;
+            // full rounds: kUnroll independent loads in flight, no per-element guard
+            for (; k + (kUnroll - 1) * G < dq; k += G * kUnroll) {
+                int w[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) w[u] = lp[k + u * G];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int h = table_lookup<MODE, PV>(tb, w[u]);
+                    if (h >= 0) {
+                        ++myc;
+                        if (PV) atomicAdd(&tb.cnts[h], 1);
+                    }
+                }
+            }
+            for (; k < dq; k += G) {
+                const int h = table_lookup<MODE, PV>(tb, lp[k]);
+                if (h >= 0) {
+                    ++myc;
+                    if (PV) atomicAdd(&tb.cnts[h], 1);
+                }
+            }
+            for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
+            if (r == 0 && valid && myc) {
+                acc += (unsigned long long)myc;
+                if (PV) atomicAdd(&a.t[sc.q[i]], (unsigned long long)myc);
             }
         }
         __syncthreads();
@@ -355,9 +386,11 @@ static int cta_table_ints(int cap, int bitmap_bits) {
     return std::max(8 * cap, bm);
 }
 
+// partners sorted per sub-chunk: 2 per thread
 static size_t cta_smem_bytes(int u_ints, int threads) {
-    return (size_t)u_ints * sizeof(int) + (size_t)threads * sizeof(int64_t) + (size_t)(threads + 1) * sizeof(int) +
-           (size_t)2 * threads * sizeof(int) + 33 * sizeof(int) + 8;
+    const int pmax = 2 * threads;
+    return (size_t)((u_ints + 1) & ~1) * sizeof(int) + (size_t)pmax * (sizeof(int64_t) + 2 * sizeof(int) + 1) +
+           (3 * kClasses + 4 + 33) * sizeof(int) + 16;
 }
 
 __device__ __forceinline__ void block_minmax(int& mn, int& mx, int* red) {
@@ -374,16 +407,22 @@ __device__ __forceinline__ void block_minmax(int& mn, int& mx, int* red) {
     __syncthreads();
 }
 
-template <bool PV, int PROBE>
-__global__ void __launch_bounds__(1024) k_count_cta(CountArgs a) {
+// BIG = false: at most 256 threads, registers capped for 5 resident CTAs per SM
+template <bool PV, int PROBE, bool BIG>
+__global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(CountArgs a) {
     extern __shared__ __align__(16) int smem[];
     int* U = smem;
     CtaScratch sc;
-    sc.base = reinterpret_cast<int64_t*>(smem + ((a.u_ints + 1) & ~1));
-    sc.ex = reinterpret_cast<int*>(sc.base + blockDim.x);
-    sc.q = sc.ex + blockDim.x + 1;
-    sc.cnt = sc.q + blockDim.x;
-    sc.scan = sc.cnt + blockDim.x;
+    const int pmax = 2 * blockDim.x;
+    sc.qb = reinterpret_cast<int64_t*>(smem + ((a.u_ints + 1) & ~1));
+    sc.q = reinterpret_cast<int*>(sc.qb + pmax);
+    sc.dq = sc.q + pmax;
+    sc.ccnt = sc.dq + pmax;
+    sc.coff = sc.ccnt + kClasses;
+    sc.toff = sc.coff + kClasses;
+    sc.misc = sc.toff + kClasses;
+    sc.scan = sc.misc + 4;
+    sc.tcls = reinterpret_cast<unsigned char*>(sc.scan + 33);
     __shared__ int s_red[64];
     __shared__ unsigned s_item;
     __shared__ unsigned long long s_acc;
@@ -478,9 +517,9 @@ __global__ void __launch_bounds__(1024) k_count_cta(CountArgs a) {
         }
         __syncthreads();
         unsigned long long acc;
-        if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, sc);
-        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, sc);
-        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, sc);
+        if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
@@ -667,7 +706,7 @@ static cudaError_t launch_tables(tc_ctx* ctx, const CountArgs& base, const tc_oc
         a.queue = queues + 1;
         a.u_ints = cta_table_ints(a.cap, a.bitmap_bits);
         const size_t smem = cta_smem_bytes(a.u_ints, tun.cta_threads);
-        auto kern = k_count_cta<PV, PROBE>;
+        auto kern = tun.cta_threads <= 256 ? k_count_cta<PV, PROBE, false> : k_count_cta<PV, PROBE, true>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tun.cta_threads, smem);
