@@ -162,6 +162,29 @@ void tc_ocsr_free(tc_ocsr* o);
  * must already be enqueued on `stream` or ordered before it. */
 void tc_ocsr_release(tc_ocsr* o, void* stream);
 
+/* ---- oriented CSR without device allocation --------------------------------
+ * The paper has no counterpart; this serves callers that cannot allocate
+ * device memory while running: serving loops with a latency budget (cudaMalloc
+ * and cudaFree may synchronise the device), processes whose HBM is already
+ * reserved in full by another allocator, and code running while a framework
+ * captures the stream into a graph that must hold no allocation nodes.
+ *
+ * tc_orient_noalloc writes the same oriented CSR as tc_build_oriented_csr
+ * followed by tc_ocsr_copy: rpp_out[n+1] (int64) and colp_out[nnz/2] (int32),
+ * both device buffers owned by the caller, N+(u) ascending.  The input is a
+ * device CSR as in tc_graph (it is not validated).  Work is enqueued on
+ * `stream` on the current device; the call allocates nothing and does not
+ * synchronise.  Its only scratch is a fixed 64 KiB device array inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits; that caps n at TC_NOALLOC_MAX_VERTICES, and larger graphs get
+ * TC_ERR_INVALID_ARG (use tc_build_oriented_csr for them).  The first call on
+ * a device looks the array's address up (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU race and must be serialised by the caller. */
+#define TC_NOALLOC_MAX_VERTICES (1LL << 24)
+tc_status tc_orient_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                            int64_t* rpp_out, int32_t* colp_out, void* stream);
+
 /* A batch of G independent graphs (no counterpart in the paper, which counts
  * one graph at a time; each graph is the problem of Sec. 3).  Graph i has
  * n_i = vtx_off[i+1]-vtx_off[i] vertices and nnz_i = edge_off[i+1]-edge_off[i]

@@ -102,7 +102,10 @@ _SIGS = {
     "tc_wait": (C.c_int, [_vp, C.c_uint64, C.c_int64, _P(tc_result)]),
     "tc_release": (C.c_int, [_vp, C.c_uint64]),
     "tc_server_get_stats": (C.c_int, [_vp, _P(tc_server_stats)]),
+    "tc_orient_noalloc": (C.c_int, [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp]),
 }
+
+TC_NOALLOC_MAX_VERTICES = 1 << 24
 
 # names the header declares (checked against the exports by the CPU tests)
 EXPORTS = tuple(_SIGS)
