@@ -70,6 +70,7 @@ static void apply_config(Tuning& t, const tc_config* c) {
     env("TC_CTA_THREADS", t.cta_threads);
     env("TC_CHUNK", t.chunk);
     env("TC_BITMAP_BITS", t.bitmap_bits);
+    env("TC_DIRECT_SPAN", t.direct_span);
     if (!c) return;
     if (c->small_max > 0) t.small_max = c->small_max;
     if (c->small_max < 0) t.small_max = 0;  // negative disables the thread-per-edge class
@@ -80,6 +81,8 @@ static void apply_config(Tuning& t, const tc_config* c) {
     if (c->chunk > 0) t.chunk = c->chunk;
     if (c->bitmap_bits > 0) t.bitmap_bits = c->bitmap_bits;
     if (c->bitmap_bits < 0) t.bitmap_bits = 0;
+    if (c->direct_span > 0) t.direct_span = c->direct_span;
+    if (c->direct_span < 0) t.direct_span = 0;
 }
 
 static bool config_ok(const Tuning& t) {
@@ -87,8 +90,8 @@ static bool config_ok(const Tuning& t) {
     return t.small_max >= 0 && t.small_max <= 64 && t.warp_max >= 2 && t.warp_max <= 1024 &&
            pow2(t.table_cap) && t.table_cap >= 16 && t.table_cap <= 4096 && t.warp_max <= t.table_cap &&
            (t.probe == 1 || t.probe == 2) && t.cta_threads >= 64 && t.cta_threads <= 1024 &&
-           t.cta_threads % 32 == 0 && t.chunk >= 1 && t.chunk <= (1 << 20) && t.bitmap_bits >= 0 &&
-           t.bitmap_bits <= 262144 && t.bitmap_bits % 32 == 0;
+           t.cta_threads % 32 == 0 && t.chunk >= 1 && t.chunk <= 32768 && t.bitmap_bits >= 0 &&
+           t.bitmap_bits <= 262144 && t.bitmap_bits % 32 == 0 && t.direct_span >= 0 && t.direct_span <= 16384;
 }
 
 static bool is_host_ptr(const void* p) {
@@ -248,6 +251,7 @@ tc_status tc_ctx_get_config(const tc_ctx* ctx, tc_config* out) {
     out->cta_threads = ctx->tun.cta_threads;
     out->chunk = ctx->tun.chunk;
     out->bitmap_bits = ctx->tun.bitmap_bits;
+    out->direct_span = ctx->tun.direct_span;
     return TC_OK;
 }
 

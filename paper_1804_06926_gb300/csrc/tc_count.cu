@@ -44,6 +44,7 @@ struct CountArgs {
     const int32_t* colr;          // oriented lists in rank ids
     const int32_t* perm;          // rank id -> vertex id
     int bitmap_bits;              // max span (rank ids) of a bitmap table; 0 = off
+    int direct_span;              // max span of a direct 16-bit cell table; 0 = off
     int u_ints;                   // ints of the table region of k_count_cta
     int64_t n;
     int cap;                      // keys per table segment
@@ -118,6 +119,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 // a ballot of the hits lets every partner lane count the hits that fall in
 // its own range of the window, so per-partner counts need no atomics.
 constexpr int kUnroll = 4;
+constexpr int kLoads = 8;   // loads in flight per lane in the CTA kernel
 
 template <bool PV, int PROBE>
 __device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, const int* keys, int* cnts, int logS,
@@ -233,6 +235,7 @@ struct CtaScratch {
 constexpr int kModeHash = 0;
 constexpr int kModeBitmap = 1;
 constexpr int kModeBsearch = 2;
+constexpr int kModeDirect = 3;   // one 16-bit cell per rank id of the span: 0 = absent, 1 + hits
 
 struct Table {
     const int* keys;
@@ -240,23 +243,34 @@ struct Table {
     int logS, len;
     const unsigned* bits;
     const unsigned short* pre;
+    unsigned short* cell;  // direct mode
     int lo, span;
 };
 
-// counter index of x (0 when !PV), or -1
+// Probe x; on a hit count it (per-vertex counter of x when PV) and return
+// true.
 template <int MODE, bool PV>
-__device__ __forceinline__ int table_lookup(const Table& t, int x) {
-    if (MODE == kModeBitmap) {
+__device__ __forceinline__ bool table_hit(const Table& t, int x) {
+    if (MODE == kModeDirect) {
         const unsigned off = (unsigned)(x - t.lo);
-        if (off >= (unsigned)t.span) return -1;
+        if (off >= (unsigned)t.span) return false;
+        if (!t.cell[off]) return false;
+        if (PV) atomicAdd(reinterpret_cast<unsigned*>(t.cell + (off & ~1u)), 1u << ((off & 1u) * 16u));
+        return true;
+    } else if (MODE == kModeBitmap) {
+        const unsigned off = (unsigned)(x - t.lo);
+        if (off >= (unsigned)t.span) return false;
         const unsigned word = t.bits[off >> 5];
         const unsigned b = off & 31u;
-        if (!((word >> b) & 1u)) return -1;
-        return PV ? (int)t.pre[off >> 5] + __popc(word & ((1u << b) - 1u)) : 0;
-    } else if (MODE == kModeHash) {
-        return table_find<kProbeHash>(t.keys, t.logS, t.len, x);
+        if (!((word >> b) & 1u)) return false;
+        if (PV) atomicAdd(&t.cnts[(int)t.pre[off >> 5] + __popc(word & ((1u << b) - 1u))], 1);
+        return true;
     } else {
-        return table_find<kProbeBsearch>(t.keys, t.logS, t.len, x);
+        const int h = MODE == kModeHash ? table_find<kProbeHash>(t.keys, t.logS, t.len, x)
+                                        : table_find<kProbeBsearch>(t.keys, t.logS, t.len, x);
+        if (h < 0) return false;
+        if (PV) atomicAdd(&t.cnts[h], 1);
+        return true;
     }
 }
 
@@ -345,27 +359,17 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             const int64_t qb = valid ? sc.qb[i] : 0;
             const int32_t* __restrict__ lp = L + qb;
             int myc = 0;
-            int k = r;
-            // full rounds: kUnroll independent loads in flight, no per-element guard
-            for (; k + (kUnroll - 1) * G < dq; k += G * kUnroll) {
-                int w[kUnroll];
+            // kLoads guarded loads in flight per lane; most lists take one round
+            for (int k = r; k < dq; k += G * kLoads) {
+                int w[kLoads];
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) w[u] = lp[k + u * G];
+                for (int u = 0; u < kLoads; ++u) {
+                    const int kk = k + u * G;
+                    w[u] = kk < dq ? lp[kk] : -1;
+                }
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int h = table_lookup<MODE, PV>(tb, w[u]);
-                    if (h >= 0) {
-                        ++myc;
-                        if (PV) atomicAdd(&tb.cnts[h], 1);
-                    }
-                }
-            }
-            for (; k < dq; k += G) {
-                const int h = table_lookup<MODE, PV>(tb, lp[k]);
-                if (h >= 0) {
-                    ++myc;
-                    if (PV) atomicAdd(&tb.cnts[h], 1);
-                }
+                for (int u = 0; u < kLoads; ++u)
+                    if (w[u] >= 0 && table_hit<MODE, PV>(tb, w[u])) ++myc;
             }
             for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
             if (r == 0 && valid && myc) {
@@ -455,14 +459,26 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
                 mx = max(mx, x);
             }
             block_minmax(mn, mx, s_red);
-            if (mx - mn < a.bitmap_bits) {
+            if (mx - mn < a.direct_span && (mx - mn + 2) / 2 <= a.u_ints) {
+                mode = kModeDirect;
+                tb.lo = mn;
+                tb.span = mx - mn + 1;
+            } else if (mx - mn < a.bitmap_bits) {
                 mode = kModeBitmap;
                 tb.lo = mn;
                 tb.span = mx - mn + 1;
             }
         }
         int nflush = 0;
-        if (mode == kModeBitmap) {
+        if (mode == kModeDirect) {
+            unsigned* cw = reinterpret_cast<unsigned*>(U);
+            tb.cell = reinterpret_cast<unsigned short*>(U);
+            const int W = (tb.span + 1) >> 1;
+            for (int i = threadIdx.x; i < W; i += blockDim.x) cw[i] = 0u;
+            __syncthreads();
+            for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell[L[lb + i] - tb.lo] = 1;
+            nflush = tb.span;
+        } else if (mode == kModeBitmap) {
             const int W = (tb.span + 31) >> 5;
             unsigned* bits = reinterpret_cast<unsigned*>(U);
             unsigned short* pre = reinterpret_cast<unsigned short*>(U + wmax);
@@ -517,14 +533,20 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
         }
         __syncthreads();
         unsigned long long acc;
-        if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
         else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
         else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
         if (PV) {
-            if (mode == kModeBitmap) {
+            if (mode == kModeDirect) {
+                for (int i = threadIdx.x; i < nflush; i += blockDim.x) {
+                    const int c = (int)tb.cell[i] - 1;
+                    if (c > 0) atomicAdd(&a.t[a.perm[tb.lo + i]], (unsigned long long)c);
+                }
+            } else if (mode == kModeBitmap) {
                 for (int i = threadIdx.x; i < nflush; i += blockDim.x) {
                     unsigned b = tb.bits[i];
                     int ord = tb.pre[i];
@@ -748,6 +770,7 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.colr = o->colr;
     a.perm = o->perm;
     a.bitmap_bits = tun.bitmap_bits;
+    a.direct_span = tun.direct_span;
     const int ns = ctx->num_sms;
 
     if (tun.small_max >= 2) {

@@ -38,6 +38,7 @@ struct Tuning {
     int cta_threads = 256;
     int chunk = 512;
     int bitmap_bits = 131072;  // CTA items whose list spans <= this many rank ids use a bitmap
+    int direct_span = 16384;   // ... and <= this many a direct 16-bit cell per rank id
 };
 
 }  // namespace tc

@@ -121,7 +121,9 @@ CONFIGS = [
     dict(cta_threads=128, chunk=7),
     dict(cta_threads=1024, table_cap=4096, warp_max=1024),
     dict(bitmap_bits=-1),
-    dict(bitmap_bits=64, warp_max=4),
+    dict(direct_span=-1),
+    dict(direct_span=-1, bitmap_bits=64, warp_max=4),
+    dict(direct_span=40, warp_max=4, chunk=9),
     dict(bitmap_bits=262144, table_cap=64, warp_max=8, chunk=5),
 ]
 
