@@ -357,8 +357,12 @@ def run_batch(args, torch, binding, dev, rank, world):
     b = gen.ba_batch(G, 100, 20000, 2, 16, seed0=rank * G)
     m_tot = int(b.edge_off[-1] // 2)
     log(f"[rank {rank}] BA batch: G={G} n={int(b.vtx_off[-1])} m={m_tot}")
-    ctx = binding.Context(dev.index)
     vo, eo, rp, col = (torch.from_numpy(x).to(dev) for x in (b.vtx_off, b.edge_off, b.row_ptr, b.col))
+    # strategy, thresholds and tile sizes for this size class, measured on the device
+    from paper_1804_06926_gb300 import autotune
+    tuned = autotune.tune_batch(vo, eo, rp, col, per_vertex=True, reps=1, device=dev.index,
+                                tuner=autotune.Autotuner(device_name=torch.cuda.get_device_name(dev)))
+    ctx = binding.Context(dev.index, **tuned.best)
     totals = torch.zeros(G, dtype=torch.int64, device=dev)
     pv = torch.zeros(int(b.vtx_off[-1]), dtype=torch.int64, device=dev)
     plan = ctx.batch_plan(vo, eo, rp, col, totals, pv)
@@ -409,6 +413,8 @@ def run_batch(args, torch, binding, dev, rank, world):
         "one_launch_per_graph": {"ms": ms_single, "edges_per_s": m_tot / (ms_single * 1e-3),
                                  "graphs_per_s": G / (ms_single * 1e-3)},
         "batch_speedup": ms_single / ms_batch,
+        "autotuned_config": tuned.best,
+        "autotune_ms": tuned.times_ms,
         "triangles_total": int(T_batch.sum()),
         "clocks": clocks,
     }

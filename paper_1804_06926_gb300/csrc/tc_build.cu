@@ -516,11 +516,12 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         if (e == cudaSuccess) e = dev_alloc(p, std::max<size_t>(b, 16), s);
     };
     A((void**)&o->rpp, sizeof(int64_t) * n1);
-    A((void**)&o->colp, sizeof(int32_t) * std::max<int64_t>(m, 1));
+    // +4: the count kernels read lists as aligned 16-byte vectors
+    A((void**)&o->colp, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 4));
     A((void**)&o->dplus, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->rank, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->perm, sizeof(int32_t) * std::max<int64_t>(n, 1));
-    A((void**)&o->colr, sizeof(int32_t) * std::max<int64_t>(m, 1));
+    A((void**)&o->colr, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 4));
     A((void**)&o->prp, sizeof(int64_t) * n1);
     A((void**)&o->pcol, sizeof(int32_t) * std::max<int64_t>(m, 1));
     A((void**)&o->items_warp, sizeof(Item) * o->items_warp_cap);

@@ -119,7 +119,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 // a ballot of the hits lets every partner lane count the hits that fall in
 // its own range of the window, so per-partner counts need no atomics.
 constexpr int kUnroll = 4;
-constexpr int kLoads = 8;   // loads in flight per lane in the CTA kernel
+constexpr int kVec = 4;     // 16-byte vector loads in flight per lane in the CTA kernel
 
 template <bool PV, int PROBE>
 __device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, const int* keys, int* cnts, int logS,
@@ -275,9 +275,9 @@ __device__ __forceinline__ bool table_hit(const Table& t, int x) {
 }
 
 // Lanes per partner for a list-length class c (lists of 2^c .. 2^(c+1)-1
-// elements): one lane up to 7 elements, then doubling up to a full warp, so
-// that every lane of a task walks about 4 to 8 elements per list.
-__device__ __forceinline__ int class_lanes(int c) { return 1 << min(max(c - 2, 0), 5); }
+// elements): one lane up to 15 elements, then doubling up to a full warp, so
+// that every lane of a task loads 2 to 4 aligned 16-byte vectors per list.
+__device__ __forceinline__ int class_lanes(int c) { return 1 << min(max(c - 3, 0), 5); }
 
 // Intersect the item's partners [pb, pe) with the table.  Partners are taken
 // pmax at a time, counting-sorted by length class, and cut into warp tasks of
@@ -357,19 +357,26 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             const bool valid = i < sc.coff[c] + sc.ccnt[c];
             const int dq = valid ? sc.dq[i] : 0;
             const int64_t qb = valid ? sc.qb[i] : 0;
-            const int32_t* __restrict__ lp = L + qb;
+            // the list as aligned int4 vectors (the lists are padded by 4 elements)
+            const int s0 = (int)(qb & 3);
+            const int4* __restrict__ lv = reinterpret_cast<const int4*>(L + (qb - s0));
+            const int nv = (s0 + dq + 3) >> 2;
             int myc = 0;
-            // kLoads guarded loads in flight per lane; most lists take one round
-            for (int k = r; k < dq; k += G * kLoads) {
-                int w[kLoads];
+            for (int v0 = r; v0 < nv; v0 += G * kVec) {
+                int4 w[kVec];
 #pragma unroll
-                for (int u = 0; u < kLoads; ++u) {
-                    const int kk = k + u * G;
-                    w[u] = kk < dq ? lp[kk] : -1;
+                for (int u = 0; u < kVec; ++u) {
+                    const int vv = v0 + u * G;
+                    w[u] = vv < nv ? lv[vv] : make_int4(0, 0, 0, 0);
                 }
 #pragma unroll
-                for (int u = 0; u < kLoads; ++u)
-                    if (w[u] >= 0 && table_hit<MODE, PV>(tb, w[u])) ++myc;
+                for (int u = 0; u < kVec; ++u) {
+                    const int j0 = 4 * (v0 + u * G) - s0;  // list position of w[u].x
+                    if ((unsigned)(j0 + 0) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].x)) ++myc;
+                    if ((unsigned)(j0 + 1) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].y)) ++myc;
+                    if ((unsigned)(j0 + 2) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].z)) ++myc;
+                    if ((unsigned)(j0 + 3) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].w)) ++myc;
+                }
             }
             for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
             if (r == 0 && valid && myc) {
