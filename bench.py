@@ -70,7 +70,7 @@ def oriented_out_degrees(g):
     return np.bincount(u[keep], minlength=g.n).astype(np.int64), deg
 
 
-def class_bytes(g, dplus, small_max=8, warp_max=64):
+def class_bytes(g, dplus, small_max=8, warp_max=128):
     """Split the per-edge list bytes 4*(d+(u)+d+(v)) over the kernels that own
     each oriented edge (the partition of tc_build_oriented_csr): thread-per-edge
     merge, warp tables, CTA tables, and edges that cannot close a triangle."""

@@ -82,7 +82,7 @@ typedef struct tc_config {
     int32_t small_max;     /* oriented edges with max(d+(u), d+(v)) <= small_max are merged by one
                               thread each (the paper's TwoSmall); default 8 */
     int32_t warp_max;      /* pivots with d+ <= warp_max probe a warp-private table; larger pivots a
-                              CTA-wide table (the paper's TwoLarge role); default 64 */
+                              CTA-wide table (the paper's TwoLarge role); default 128 */
     int32_t table_cap;     /* keys per CTA table segment (power of two, 16..4096); longer lists are
                               split into segments; default 1024 */
     int32_t probe;         /* 0/1 = open-addressing hash probe, 2 = binary search of the sorted list */

@@ -88,7 +88,7 @@ static void apply_config(Tuning& t, const tc_config* c) {
 static bool config_ok(const Tuning& t) {
     auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
     return t.small_max >= 0 && t.small_max <= 64 && t.warp_max >= 2 && t.warp_max <= 1024 &&
-           pow2(t.table_cap) && t.table_cap >= 16 && t.table_cap <= 4096 && t.warp_max <= t.table_cap &&
+           pow2(t.table_cap) && t.table_cap >= 16 && t.table_cap <= 4096 &&
            (t.probe == 1 || t.probe == 2) && t.cta_threads >= 64 && t.cta_threads <= 1024 &&
            t.cta_threads % 32 == 0 && t.chunk >= 1 && t.chunk <= 32768 && t.bitmap_bits >= 0 &&
            t.bitmap_bits <= 262144 && t.bitmap_bits % 32 == 0 && t.direct_span >= 0 && t.direct_span <= 16384;
@@ -144,7 +144,7 @@ static tc_status count_any(tc_ctx* ctx, const tc_ocsr* o, int64_t* totals, int64
 
 static void release_ocsr(tc_ocsr* o, cudaStream_t s, bool async) {
     if (!o) return;
-    void* ptrs[] = {o->rpp,  o->colp, o->dplus,      o->rank,      o->perm, o->colr,
+    void* ptrs[] = {o->rpp,  o->colp, o->dplus,      o->rank,      o->perm, o->colr,     o->rspan,
                     o->prp, o->pcol, o->items_warp, o->items_cta, o->dc,   o->row_graph};
     int prev = 0;
     cudaGetDevice(&prev);

@@ -213,7 +213,9 @@ template <int GS, bool SCATTER, bool BATCH>
 __global__ void __launch_bounds__(256) k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                 const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
                                                 const int64_t* __restrict__ vtx_off, int32_t* __restrict__ cnt,
-                                                const int64_t* __restrict__ rpp, int32_t* __restrict__ colp) {
+                                                const int64_t* __restrict__ rpp, int32_t* __restrict__ colp,
+                                                const int32_t* __restrict__ rank, int32_t* __restrict__ colr,
+                                                int2* __restrict__ rspan) {
     const int lane = threadIdx.x & 31;
     const int sub = lane % GS;
     const int shift = (lane / GS) * GS;
@@ -223,12 +225,16 @@ __global__ void __launch_bounds__(256) k_orient(int64_t n, const int64_t* __rest
         const int64_t b = rp[u], e = rp[u + 1];
         const int du = (int)(e - b);
         if (du > kBigRow) {  // long rows are cut into chunks for k_orient_big
-            if (!SCATTER && sub == 0) cnt[u] = 0;
+            if (!SCATTER && sub == 0) {
+                cnt[u] = 0;
+                rspan[u] = make_int2(0x7fffffff, -1);
+            }
             continue;
         }
         const int64_t base = BATCH ? vtx_off[row_graph[u]] : 0;
         int kept = 0;
         int64_t out = 0;
+        int rmin = 0x7fffffff, rmax = -1;
         if (SCATTER) out = rpp[u];
         for (int64_t j0 = b; j0 < e; j0 += GS) {
             const int64_t i = j0 + sub;
@@ -238,10 +244,25 @@ __global__ void __launch_bounds__(256) k_orient(int64_t n, const int64_t* __rest
             const bool keep = valid && (du < dv || (du == dv && u < v));
             const unsigned bal = __ballot_sync(gm, keep);
             const unsigned mine = (GS == 32) ? bal : ((bal >> shift) & ((1u << (GS & 31)) - 1u));
-            if (SCATTER && keep) colp[out + kept + __popc(mine & ((1u << sub) - 1u))] = (int32_t)v;
+            if (SCATTER && keep) {
+                const int64_t pos = out + kept + __popc(mine & ((1u << sub) - 1u));
+                const int r = rank[v];
+                colp[pos] = (int32_t)v;
+                colr[pos] = r;
+                rmin = min(rmin, r);
+                rmax = max(rmax, r);
+            }
             kept += __popc(mine);
         }
         if (!SCATTER && sub == 0) cnt[u] = kept;
+        if (SCATTER) {  // span of the row in rank ids
+#pragma unroll
+            for (int o = GS / 2; o; o >>= 1) {
+                rmin = min(rmin, __shfl_xor_sync(gm, rmin, o));
+                rmax = max(rmax, __shfl_xor_sync(gm, rmax, o));
+            }
+            if (sub == 0) rspan[u] = make_int2(rmin, rmax);
+        }
     }
 }
 
@@ -272,7 +293,8 @@ __global__ void __launch_bounds__(256) k_orient_big(const BigChunk* __restrict__
                                                     const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
                                                     const int64_t* __restrict__ vtx_off, int32_t* __restrict__ cnt,
                                                     int32_t* __restrict__ chunk_cnt, const int64_t* __restrict__ rpp,
-                                                    int32_t* __restrict__ colp) {
+                                                    int32_t* __restrict__ colp, const int32_t* __restrict__ rank,
+                                                    int32_t* __restrict__ colr, int2* __restrict__ rspan) {
     __shared__ int s_w[8];
     __shared__ long long s_off;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -290,6 +312,7 @@ __global__ void __launch_bounds__(256) k_orient_big(const BigChunk* __restrict__
             s_off = off;
         }
         int run = 0;
+        int rmin = 0x7fffffff, rmax = -1;
         for (int64_t r0 = b; r0 < e; r0 += blockDim.x) {
             const int64_t i = r0 + threadIdx.x;
             const bool valid = i < e;
@@ -305,9 +328,26 @@ __global__ void __launch_bounds__(256) k_orient_big(const BigChunk* __restrict__
                 if (k < w) before += c2;
                 tot += c2;
             }
-            if (SCATTER && keep) colp[s_off + run + before + __popc(bal & ((1u << lane) - 1u))] = (int32_t)v;
+            if (SCATTER && keep) {
+                const int64_t pos = s_off + run + before + __popc(bal & ((1u << lane) - 1u));
+                const int r = rank[v];
+                colp[pos] = (int32_t)v;
+                colr[pos] = r;
+                rmin = min(rmin, r);
+                rmax = max(rmax, r);
+            }
             run += tot;
             __syncthreads();
+        }
+        if (SCATTER) {
+            for (int o = 16; o; o >>= 1) {
+                rmin = min(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+                rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+            }
+            if (lane == 0 && rmax >= 0) {
+                atomicMin(&rspan[u].x, rmin);
+                atomicMax(&rspan[u].y, rmax);
+            }
         }
         if (!SCATTER && threadIdx.x == 0) {
             chunk_cnt[c] = run;
@@ -456,12 +496,12 @@ static unsigned grid_for(int64_t work, int threads, int num_sms, int per_sm = 8)
 template <bool SCATTER, bool BATCH>
 static void launch_orient(int gs, unsigned grid, cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* col,
                           const int32_t* deg, const int32_t* rg, const int64_t* vo, int32_t* cnt, const int64_t* rpp,
-                          int32_t* colp) {
+                          int32_t* colp, const int32_t* rank, int32_t* colr, int2* rspan) {
     switch (gs) {
-        case 4: k_orient<4, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp); break;
-        case 8: k_orient<8, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp); break;
-        case 16: k_orient<16, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp); break;
-        default: k_orient<32, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp); break;
+        case 4: k_orient<4, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp, rank, colr, rspan); break;
+        case 8: k_orient<8, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp, rank, colr, rspan); break;
+        case 16: k_orient<16, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp, rank, colr, rspan); break;
+        default: k_orient<32, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp, rank, colr, rspan); break;
     }
 }
 
@@ -522,6 +562,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     A((void**)&o->rank, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->perm, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->colr, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 4));
+    A((void**)&o->rspan, sizeof(int2) * std::max<int64_t>(n, 1));
     A((void**)&o->prp, sizeof(int64_t) * n1);
     A((void**)&o->pcol, sizeof(int32_t) * std::max<int64_t>(m, 1));
     A((void**)&o->items_warp, sizeof(Item) * o->items_warp_cap);
@@ -536,7 +577,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         dev_free(deg, s); dev_free(pc, s); dev_free(scan_tmp, s);
         return set_err(ctx, TC_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
-    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 3 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
+    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 5 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
                          + (batch ? sizeof(int32_t) * n : 0));
     cudaMemsetAsync(o->dc, 0, sizeof(DevCounters), s);
 
@@ -612,10 +653,10 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         PhaseScope ph(ctx, kPhOrientCount, s);
         cudaMemsetAsync(nbc, 0, sizeof(unsigned long long), s);
         if (n > 0) k_big_chunks<<<grid_for(n, 256, ns), 256, 0, s>>>(n, row_ptr, bchunks, bc_cap, nbc);
-        if (batch) launch_orient<false, true>(gs, og, s, n, row_ptr, col, deg, o->row_graph, vtx_off, o->dplus, nullptr, nullptr);
-        else launch_orient<false, false>(gs, og, s, n, row_ptr, col, deg, nullptr, nullptr, o->dplus, nullptr, nullptr);
-        if (batch) k_orient_big<false, true><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, o->row_graph, vtx_off, o->dplus, bcnt, nullptr, nullptr);
-        else k_orient_big<false, false><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, nullptr, nullptr, o->dplus, bcnt, nullptr, nullptr);
+        if (batch) launch_orient<false, true>(gs, og, s, n, row_ptr, col, deg, o->row_graph, vtx_off, o->dplus, nullptr, nullptr, nullptr, nullptr, o->rspan);
+        else launch_orient<false, false>(gs, og, s, n, row_ptr, col, deg, nullptr, nullptr, o->dplus, nullptr, nullptr, nullptr, nullptr, o->rspan);
+        if (batch) k_orient_big<false, true><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, o->row_graph, vtx_off, o->dplus, bcnt, nullptr, nullptr, nullptr, nullptr, nullptr);
+        else k_orient_big<false, false><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, nullptr, nullptr, o->dplus, bcnt, nullptr, nullptr, nullptr, nullptr, nullptr);
         ctx->launches += 3;
     }
     // a-3: row offsets of the oriented CSR, then the stable scatter
@@ -626,20 +667,15 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     }
     {
         PhaseScope ph(ctx, kPhOrientScatter, s);
-        if (batch) launch_orient<true, true>(gs, og, s, n, row_ptr, col, deg, o->row_graph, vtx_off, nullptr, o->rpp, o->colp);
-        else launch_orient<true, false>(gs, og, s, n, row_ptr, col, deg, nullptr, nullptr, nullptr, o->rpp, o->colp);
-        if (batch) k_orient_big<true, true><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, o->row_graph, vtx_off, nullptr, bcnt, o->rpp, o->colp);
-        else k_orient_big<true, false><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, nullptr, nullptr, nullptr, bcnt, o->rpp, o->colp);
+        if (batch) launch_orient<true, true>(gs, og, s, n, row_ptr, col, deg, o->row_graph, vtx_off, nullptr, o->rpp, o->colp, o->rank, o->colr, o->rspan);
+        else launch_orient<true, false>(gs, og, s, n, row_ptr, col, deg, nullptr, nullptr, nullptr, o->rpp, o->colp, o->rank, o->colr, o->rspan);
+        if (batch) k_orient_big<true, true><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, o->row_graph, vtx_off, nullptr, bcnt, o->rpp, o->colp, o->rank, o->colr, o->rspan);
+        else k_orient_big<true, false><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, nullptr, nullptr, nullptr, bcnt, o->rpp, o->colp, o->rank, o->colr, o->rspan);
         ctx->launches += 2;
     }
     dev_free(bchunks, s);
     dev_free(bcnt, s);
     dev_free(nbc, s);
-    if (m > 0) {
-        PhaseScope ph(ctx, kPhRelabel, s);
-        k_relabel<<<grid_for(m, 256, ns, 16), 256, 0, s>>>(m, o->colp, o->rank, o->colr);
-        TC_LAUNCH(ctx);
-    }
     // a-4: classify, group oriented edges by pivot, cut work items
     const int gs2 = pick_group(n, m);
     const unsigned pg = grid_for(n * gs2, 256, ns, 16);

@@ -43,6 +43,7 @@ struct CountArgs {
     const int32_t* row_graph;     // batch: graph of each vertex, else nullptr
     const int32_t* colr;          // oriented lists in rank ids
     const int32_t* perm;          // rank id -> vertex id
+    const int2* rspan;            // smallest and largest rank id of each oriented row
     int bitmap_bits;              // max span (rank ids) of a bitmap table; 0 = off
     int direct_span;              // max span of a direct 16-bit cell table; 0 = off
     int u_ints;                   // ints of the table region of k_count_cta
@@ -119,7 +120,13 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 // a ballot of the hits lets every partner lane count the hits that fall in
 // its own range of the window, so per-partner counts need no atomics.
 constexpr int kUnroll = 4;
-constexpr int kVec = 4;     // 16-byte vector loads in flight per lane in the CTA kernel
+#ifndef TC_CTA_VEC
+#define TC_CTA_VEC 4
+#endif
+#ifndef TC_CTA_LANE_SHIFT
+#define TC_CTA_LANE_SHIFT 3
+#endif
+constexpr int kVec = TC_CTA_VEC;  // 16-byte vector loads in flight per lane in the CTA kernel
 
 template <bool PV, int PROBE>
 __device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, const int* keys, int* cnts, int logS,
@@ -277,7 +284,7 @@ __device__ __forceinline__ bool table_hit(const Table& t, int x) {
 // Lanes per partner for a list-length class c (lists of 2^c .. 2^(c+1)-1
 // elements): one lane up to 15 elements, then doubling up to a full warp, so
 // that every lane of a task loads 2 to 4 aligned 16-byte vectors per list.
-__device__ __forceinline__ int class_lanes(int c) { return 1 << min(max(c - 3, 0), 5); }
+__device__ __forceinline__ int class_lanes(int c) { return 1 << min(max(c - TC_CTA_LANE_SHIFT, 0), 5); }
 
 // Intersect the item's partners [pb, pe) with the table.  Partners are taken
 // pmax at a time, counting-sorted by length class, and cut into warp tasks of
@@ -435,37 +442,62 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
     sc.scan = sc.misc + 4;
     sc.tcls = reinterpret_cast<unsigned char*>(sc.scan + 33);
     __shared__ int s_red[64];
-    __shared__ unsigned s_item;
     __shared__ unsigned long long s_acc;
+    // the next work item, fetched one iteration ahead by thread 0 so that the
+    // queue atomic and the dependent descriptor loads overlap the current item
+    __shared__ Item s_cur;
+    __shared__ long long s_r0, s_r1;
+    __shared__ int s_valid;
     const int lane = threadIdx.x & 31;
     // hash mode probes rank ids (so that a short span can use the bitmap);
     // the binary-search mode probes the id-sorted lists
     const int32_t* __restrict__ L = PROBE == kProbeHash ? a.colr : a.colp;
     const unsigned long long n_items = min(*a.n_items, a.items_cap);
     const int wmax = a.bitmap_bits / 32;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_item = atomicAdd(a.queue, 1u);
-            s_acc = 0;
+    if (threadIdx.x == 0) {
+        const unsigned it = atomicAdd(a.queue, 1u);
+        s_valid = it < n_items;
+        if (s_valid) {
+            s_cur = a.items[it];
+            s_r0 = a.rpp[s_cur.p];
+            s_r1 = a.rpp[s_cur.p + 1];
         }
+    }
+    for (;;) {
         __syncthreads();
-        const unsigned it = s_item;
-        if (it >= n_items) break;
-        const Item item = a.items[it];
+        if (!s_valid) break;
+        const Item item = s_cur;
         const int p = item.p;
-        const int64_t lb = a.rpp[p] + (int64_t)item.seg * a.cap;
-        const int len = (int)min((int64_t)a.cap, a.rpp[p + 1] - lb);
+        const int64_t r0 = s_r0, r1 = s_r1;
+        __syncthreads();  // everyone has read the current item
+        unsigned nit = 0;
+        Item nitem{};
+        if (threadIdx.x == 0) {
+            s_acc = 0;
+            nit = atomicAdd(a.queue, 1u);
+            if (nit < n_items) nitem = a.items[nit];
+        }
+        const int64_t lb = r0 + (int64_t)item.seg * a.cap;
+        const int len = (int)min((int64_t)a.cap, r1 - lb);
         Table tb{};
         tb.len = len;
         int mode = PROBE == kProbeHash ? kModeHash : kModeBsearch;
         if (PROBE == kProbeHash && a.bitmap_bits > 0) {
-            int mn = 0x7fffffff, mx = -1;
-            for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                const int x = L[lb + i];
-                mn = min(mn, x);
-                mx = max(mx, x);
+            int mn, mx;
+            if (r1 - r0 == len) {  // the whole row: its span is known
+                const int2 sp = a.rspan[p];
+                mn = sp.x;
+                mx = sp.y;
+            } else {
+                mn = 0x7fffffff;
+                mx = -1;
+                for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                    const int x = L[lb + i];
+                    mn = min(mn, x);
+                    mx = max(mx, x);
+                }
+                block_minmax(mn, mx, s_red);
             }
-            block_minmax(mn, mx, s_red);
             if (mx - mn < a.direct_span && (mx - mn + 2) / 2 <= a.u_ints) {
                 mode = kModeDirect;
                 tb.lo = mn;
@@ -575,12 +607,19 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
                 }
             }
         }
-        if (threadIdx.x == 0 && s_acc) {
-            const int g = a.row_graph ? a.row_graph[p] : 0;
-            atomicAdd(&a.totals[g], s_acc);
-            if (PV) atomicAdd(&a.t[p], s_acc);
+        if (threadIdx.x == 0) {
+            if (s_acc) {
+                const int g = a.row_graph ? a.row_graph[p] : 0;
+                atomicAdd(&a.totals[g], s_acc);
+                if (PV) atomicAdd(&a.t[p], s_acc);
+            }
+            s_valid = nit < n_items;
+            if (s_valid) {
+                s_cur = nitem;
+                s_r0 = a.rpp[nitem.p];
+                s_r1 = a.rpp[nitem.p + 1];
+            }
         }
-        __syncthreads();
     }
 }
 
@@ -776,6 +815,7 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.small_max = tun.small_max;
     a.colr = o->colr;
     a.perm = o->perm;
+    a.rspan = o->rspan;
     a.bitmap_bits = tun.bitmap_bits;
     a.direct_span = tun.direct_span;
     const int ns = ctx->num_sms;

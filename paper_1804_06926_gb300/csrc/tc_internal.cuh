@@ -32,7 +32,7 @@ struct __align__(16) Item {
 
 struct Tuning {
     int small_max = 8;
-    int warp_max = 64;
+    int warp_max = 128;
     int table_cap = 1024;
     int probe = 1;          // 1 hash, 2 binary search
     int cta_threads = 256;
@@ -53,6 +53,7 @@ struct tc_ocsr {
     int32_t* rank = nullptr;    // [n] position of each vertex in (degree, id) order
     int32_t* perm = nullptr;    // [n] inverse of rank
     int32_t* colr = nullptr;    // [m] colp relabelled to rank ids (same row layout)
+    int2* rspan = nullptr;      // [n] smallest and largest rank id in each oriented row
     int64_t* prp = nullptr;     // [n+1] partner row offsets
     int32_t* pcol = nullptr;    // [m] partners (only the first n_pivot_edges used)
     tc::Item* items_warp = nullptr;
