@@ -6,6 +6,7 @@
 // Partition, Sec. 4.2.2 (dynamic grouping by list size).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "tc_internal.cuh"
 
@@ -479,7 +480,11 @@ __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restr
 // ============================================================================
 // host side
 // ============================================================================
-static int pick_group(int64_t n, int64_t entries) {
+static int pick_group(int64_t n, int64_t entries, const char* env_name) {
+    if (const char* v = std::getenv(env_name)) {  // tuning override: 4, 8, 16 or 32 lanes per row
+        const int g = std::atoi(v);
+        if (g == 4 || g == 8 || g == 16 || g == 32) return g;
+    }
     double avg = n > 0 ? (double)entries / (double)n : 0.0;
     if (avg <= 4.0) return 4;
     if (avg <= 8.0) return 8;
@@ -619,7 +624,9 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         if (e == cudaSuccess) e = dev_alloc((void**)&kb, sizeof(unsigned long long) * n, s);
         if (e == cudaSuccess) {
             k_rank_keys<<<grid_for(n, 256, ns), 256, 0, s>>>(n, deg, b, ka);
-            radix_sort_u64(ka, kb, n, 2 * b, s, &sorted, &ctx->launches);
+            // the keys are written in id order and the sort is stable, so
+            // sorting the degree bits alone yields (degree, id) order
+            radix_sort_u64(ka, kb, n, 2 * b, s, &sorted, &ctx->launches, b);
             k_rank_from_sorted<<<grid_for(n, 256, ns), 256, 0, s>>>(n, sorted, b, o->rank, o->perm);
             ctx->launches += 2;
         }
@@ -631,7 +638,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
             return set_err(ctx, TC_ERR_OOM, "rank: device allocation failed");
         }
     }
-    const int gs = pick_group(n, nnz);
+    const int gs = pick_group(n, nnz, "TC_ORIENT_GROUP");
     const unsigned og = grid_for(n * gs, 256, ns, 16);
     // long rows: chunk list (bounded by nnz/kBigChunk + nnz/kBigRow)
     const int64_t bc_cap = nnz / kBigChunk + nnz / kBigRow + 2;
@@ -677,7 +684,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     dev_free(bcnt, s);
     dev_free(nbc, s);
     // a-4: classify, group oriented edges by pivot, cut work items
-    const int gs2 = pick_group(n, m);
+    const int gs2 = pick_group(n, m, "TC_PIVOT_GROUP");
     const unsigned pg = grid_for(n * gs2, 256, ns, 16);
     {
         PhaseScope ph(ctx, kPhPivotCount, s);

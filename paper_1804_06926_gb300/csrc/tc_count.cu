@@ -107,89 +107,14 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
     return x;
 }
 
-// One warp intersects the partners pb+first, pb+first+stride, ... (in groups
-// of 32, one partner per lane) with the table.
-//
-// The lists of the 32 partners are flattened into one sequence of
-// tot = sum d+(q) elements; window k0 .. k0+31 puts element k0+lane on lane
-// `lane`.  The owner of an element is found without a search: every partner
-// marks the position where its list starts (all partner lists are non-empty,
-// the partition guarantees it), the marks of a window are OR-reduced into a
-// bit mask M, and the owner of position lane is (partners started before the
-// window) + popc(M & lanes <= lane) - 1.  Each element is probed in the table;
-// a ballot of the hits lets every partner lane count the hits that fall in
-// its own range of the window, so per-partner counts need no atomics.
-constexpr int kUnroll = 4;
 #ifndef TC_CTA_VEC
 #define TC_CTA_VEC 4
 #endif
 #ifndef TC_CTA_LANE_SHIFT
 #define TC_CTA_LANE_SHIFT 3
 #endif
-constexpr int kVec = TC_CTA_VEC;  // 16-byte vector loads in flight per lane in the CTA kernel
+constexpr int kVec = TC_CTA_VEC;  // 16-byte vector loads in flight per lane
 
-template <bool PV, int PROBE>
-__device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, const int* keys, int* cnts, int logS,
-                                                            int len, int64_t pbase, int pb, int pe, int first,
-                                                            int stride) {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const unsigned le_mask = lane == 31 ? FULL : ((2u << lane) - 1u);
-    unsigned long long acc = 0;
-    for (int g0 = pb + first; g0 < pe; g0 += stride) {
-        const int i = g0 + lane;
-        const bool valid = i < pe;
-        const int q = valid ? a.pcol[pbase + i] : 0;
-        const int64_t qb = valid ? a.rpp[q] : 0;
-        const int dq = valid ? (int)(a.rpp[q + 1] - qb) : 0;
-        const int incl = warp_incl_scan_i(dq);
-        const int tot = __shfl_sync(FULL, incl, 31);
-        const int excl = incl - dq;
-        const int64_t base = qb - excl;  // element k of partner q sits at colp[base + k]
-        int myc = 0, P = 0;
-        for (int k0 = 0; k0 < tot; k0 += 32 * kUnroll) {
-            int w[kUnroll];
-            bool in[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int s = excl - (k0 + 32 * u);
-                const unsigned bit = (valid && s >= 0 && s < 32) ? (1u << s) : 0u;
-                const unsigned M = __reduce_or_sync(FULL, bit);
-                const int j = P + __popc(M & le_mask) - 1;
-                P += __popc(M);
-                const int64_t bj = __shfl_sync(FULL, base, j & 31);
-                const int k = k0 + 32 * u + lane;
-                in[u] = k < tot;
-                w[u] = in[u] ? a.colp[bj + k] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                bool hit = false;
-                if (in[u]) {
-                    const int h = table_find<PROBE>(keys, logS, len, w[u]);
-                    if (h >= 0) {
-                        hit = true;
-                        if (PV) atomicAdd(&cnts[h], 1);
-                    }
-                }
-                const unsigned hm = __ballot_sync(FULL, hit);
-                if (hm) {
-                    const int s = excl - (k0 + 32 * u);
-                    const int lo = max(s, 0), hi = min(s + dq, 32);
-                    if (lo < hi) {
-                        const unsigned rm = (hi >= 32 ? FULL : ((1u << hi) - 1u)) & (FULL << lo);
-                        myc += __popc(hm & rm);
-                    }
-                }
-            }
-        }
-        if (valid && myc) {
-            acc += (unsigned long long)myc;
-            if (PV) atomicAdd(&a.t[q], (unsigned long long)myc);
-        }
-    }
-    return acc;
-}
 
 // ---------------------------------------------------------------------------
 // CTA-table kernel (persistent; items from a global queue)
@@ -286,6 +211,113 @@ __device__ __forceinline__ bool table_hit(const Table& t, int x) {
 // that every lane of a task loads 2 to 4 aligned 16-byte vectors per list.
 __device__ __forceinline__ int class_lanes(int c) { return 1 << min(max(c - TC_CTA_LANE_SHIFT, 0), 5); }
 
+// One warp intersects the partners pb+first, pb+first+stride, ... (in groups
+// of 32, one partner per lane) with the table.
+//
+// The lists of the 32 partners are flattened into one sequence of
+// tot = sum d+(q) elements; window k0 .. k0+31 puts element k0+lane on lane
+// `lane`.  The owner of an element is found without a search: every partner
+// marks the position where its list starts (all partner lists are non-empty,
+// the partition guarantees it), the marks of a window are OR-reduced into a
+// bit mask M, and the owner of position lane is (partners started before the
+// window) + popc(M & lanes <= lane) - 1.  Each element is probed in the table;
+// a ballot of the hits lets every partner lane count the hits that fall in
+// its own range of the window, so per-partner counts need no atomics.
+constexpr int kUnroll = 4;
+
+template <bool PV, int PROBE>
+__device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, const int* keys, int* cnts, int logS,
+                                                            int len, int64_t pbase, int pb, int pe, int first,
+                                                            int stride) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned le_mask = lane == 31 ? FULL : ((2u << lane) - 1u);
+    unsigned long long acc = 0;
+    for (int g0 = pb + first; g0 < pe; g0 += stride) {
+        const int i = g0 + lane;
+        const bool valid = i < pe;
+        const int q = valid ? a.pcol[pbase + i] : 0;
+        const int64_t qb = valid ? a.rpp[q] : 0;
+        const int dq = valid ? (int)(a.rpp[q + 1] - qb) : 0;
+        const int incl = warp_incl_scan_i(dq);
+        const int tot = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - dq;
+        const int64_t base = qb - excl;  // element k of partner q sits at colp[base + k]
+        int myc = 0, P = 0;
+        for (int k0 = 0; k0 < tot; k0 += 32 * kUnroll) {
+            int w[kUnroll];
+            bool in[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int s = excl - (k0 + 32 * u);
+                const unsigned bit = (valid && s >= 0 && s < 32) ? (1u << s) : 0u;
+                const unsigned M = __reduce_or_sync(FULL, bit);
+                const int j = P + __popc(M & le_mask) - 1;
+                P += __popc(M);
+                const int64_t bj = __shfl_sync(FULL, base, j & 31);
+                const int k = k0 + 32 * u + lane;
+                in[u] = k < tot;
+                w[u] = in[u] ? a.colp[bj + k] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                bool hit = false;
+                if (in[u]) {
+                    const int h = table_find<PROBE>(keys, logS, len, w[u]);
+                    if (h >= 0) {
+                        hit = true;
+                        if (PV) atomicAdd(&cnts[h], 1);
+                    }
+                }
+                const unsigned hm = __ballot_sync(FULL, hit);
+                if (hm) {
+                    const int s = excl - (k0 + 32 * u);
+                    const int lo = max(s, 0), hi = min(s + dq, 32);
+                    if (lo < hi) {
+                        const unsigned rm = (hi >= 32 ? FULL : ((1u << hi) - 1u)) & (FULL << lo);
+                        myc += __popc(hm & rm);
+                    }
+                }
+            }
+        }
+        if (valid && myc) {
+            acc += (unsigned long long)myc;
+            if (PV) atomicAdd(&a.t[q], (unsigned long long)myc);
+        }
+    }
+    return acc;
+}
+
+// Lane r of the G lanes that share one partner list (start qb, length dq in
+// L) probes the list's elements in the table, reading the list as aligned
+// 16-byte vectors r, r+G, ... (the lists are padded by 4 elements), kVec
+// vectors in flight.  Returns this lane's hits.
+template <int MODE, bool PV>
+__device__ __forceinline__ int probe_list(const Table& tb, const int32_t* __restrict__ L, int64_t qb, int dq, int r,
+                                          int G) {
+    const int s0 = (int)(qb & 3);
+    const int4* __restrict__ lv = reinterpret_cast<const int4*>(L + (qb - s0));
+    const int nv = (s0 + dq + 3) >> 2;
+    int myc = 0;
+    for (int v0 = r; v0 < nv; v0 += G * kVec) {
+        int4 w[kVec];
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int vv = v0 + u * G;
+            w[u] = vv < nv ? lv[vv] : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int j0 = 4 * (v0 + u * G) - s0;  // list position of w[u].x
+            if ((unsigned)(j0 + 0) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].x)) ++myc;
+            if ((unsigned)(j0 + 1) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].y)) ++myc;
+            if ((unsigned)(j0 + 2) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].z)) ++myc;
+            if ((unsigned)(j0 + 3) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].w)) ++myc;
+        }
+    }
+    return myc;
+}
+
 // Intersect the item's partners [pb, pe) with the table.  Partners are taken
 // pmax at a time, counting-sorted by length class, and cut into warp tasks of
 // 32/G partners of one class with G lanes per partner (the dynamic grouping by
@@ -364,27 +396,7 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             const bool valid = i < sc.coff[c] + sc.ccnt[c];
             const int dq = valid ? sc.dq[i] : 0;
             const int64_t qb = valid ? sc.qb[i] : 0;
-            // the list as aligned int4 vectors (the lists are padded by 4 elements)
-            const int s0 = (int)(qb & 3);
-            const int4* __restrict__ lv = reinterpret_cast<const int4*>(L + (qb - s0));
-            const int nv = (s0 + dq + 3) >> 2;
-            int myc = 0;
-            for (int v0 = r; v0 < nv; v0 += G * kVec) {
-                int4 w[kVec];
-#pragma unroll
-                for (int u = 0; u < kVec; ++u) {
-                    const int vv = v0 + u * G;
-                    w[u] = vv < nv ? lv[vv] : make_int4(0, 0, 0, 0);
-                }
-#pragma unroll
-                for (int u = 0; u < kVec; ++u) {
-                    const int j0 = 4 * (v0 + u * G) - s0;  // list position of w[u].x
-                    if ((unsigned)(j0 + 0) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].x)) ++myc;
-                    if ((unsigned)(j0 + 1) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].y)) ++myc;
-                    if ((unsigned)(j0 + 2) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].z)) ++myc;
-                    if ((unsigned)(j0 + 3) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].w)) ++myc;
-                }
-            }
+            int myc = probe_list<MODE, PV>(tb, L, qb, dq, r, G);
             for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
             if (r == 0 && valid && myc) {
                 acc += (unsigned long long)myc;

@@ -119,9 +119,9 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
                                 const int32_t* col, const int64_t* vtx_off, int64_t G,
                                 bool validate, tc_ocsr** out, cudaStream_t s);
 
-// Stable LSD radix sort of uint64 keys on their low key_bits bits.
+// Stable LSD radix sort of uint64 keys on bits [low_bit, key_bits).
 cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64_t K, int key_bits, cudaStream_t s,
-                           unsigned long long** sorted, long long* launches);
+                           unsigned long long** sorted, long long* launches, int low_bit);
 
 // Canonicalise a device edge list into a device CSR (library-owned buffers).
 tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t npairs, const int32_t* src, const int32_t* dst,

@@ -93,11 +93,11 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long l
     }
 }
 
-// LSD radix sort of K keys on their low key_bits bits (8 bits per pass,
+// LSD radix sort of K keys on bits [low_bit, key_bits) (8 bits per pass,
 // stable).  ka holds the input, kb is scratch of the same size; *sorted
 // receives whichever of the two holds the result.
 cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64_t K, int key_bits, cudaStream_t s,
-                           unsigned long long** sorted, long long* launches) {
+                           unsigned long long** sorted, long long* launches, int low_bit) {
     *sorted = ka;
     if (K <= 0) return cudaSuccess;
     const int64_t ntiles = (K + kRsTile - 1) / kRsTile;
@@ -110,7 +110,7 @@ cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64
     if (e == cudaSuccess) e = dev_alloc((void**)&hoff, sizeof(int64_t) * (nh + 1), s);
     if (e == cudaSuccess) e = dev_alloc(&stmp, stb, s);
     if (e == cudaSuccess) {
-        for (int shift = 0; shift < key_bits; shift += 8) {
+        for (int shift = low_bit; shift < key_bits; shift += 8) {
             k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, K, shift, hist, ntiles);
             scan_i32_to_i64(hist, hoff, nh, stmp, stb, s);
             k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, kb, K, shift, hoff, ntiles);
@@ -218,7 +218,7 @@ tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t np, const int32_t* src, c
     if (np > 0) k_make_keys<<<grid, 256, 0, s>>>(np, src, dst, n, b, sentinel, ka, err);
     {
         unsigned long long* sorted = ka;
-        radix_sort_u64(ka, kb, K, key_bits, s, &sorted, nullptr);
+        radix_sort_u64(ka, kb, K, key_bits, s, &sorted, nullptr, 0);
         if (sorted != ka) std::swap(ka, kb);
     }
     if (K > 0) k_mark_unique<<<grid, 256, 0, s>>>(ka, K, sentinel, flag);
