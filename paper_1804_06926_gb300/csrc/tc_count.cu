@@ -69,6 +69,29 @@ __device__ __forceinline__ void table_insert(int* keys, int logS, int x) {
     }
 }
 
+// Zero-encoded open addressing for the CTA tables: a slot holds x+1, 0 is
+// empty, so a table whose slots are reset after use is all zeros again.
+__device__ __forceinline__ void table_insert_z(int* keys, int logS, int x) {
+    const unsigned mask = (1u << logS) - 1u;
+    unsigned h = hslot(x, logS);
+    while (true) {
+        const int prev = atomicCAS(&keys[h], 0, x + 1);
+        if (prev == 0) return;
+        h = (h + 1u) & mask;
+    }
+}
+
+__device__ __forceinline__ int table_find_z(const int* keys, int logS, int x) {
+    const unsigned mask = (1u << logS) - 1u;
+    unsigned h = hslot(x, logS);
+    while (true) {
+        const int k = keys[h];
+        if (k == x + 1) return (int)h;
+        if (k == 0) return -1;
+        h = (h + 1u) & mask;
+    }
+}
+
 // slot of x, or -1
 template <int PROBE>
 __device__ __forceinline__ int table_find(const int* keys, int logS, int len, int x) {
@@ -198,7 +221,7 @@ __device__ __forceinline__ bool table_hit(const Table& t, int x) {
         if (PV) atomicAdd(&t.cnts[(int)t.pre[off >> 5] + __popc(word & ((1u << b) - 1u))], 1);
         return true;
     } else {
-        const int h = MODE == kModeHash ? table_find<kProbeHash>(t.keys, t.logS, t.len, x)
+        const int h = MODE == kModeHash ? table_find_z(t.keys, t.logS, x)
                                         : table_find<kProbeBsearch>(t.keys, t.logS, t.len, x);
         if (h < 0) return false;
         if (PV) atomicAdd(&t.cnts[h], 1);
@@ -466,6 +489,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
     const int32_t* __restrict__ L = PROBE == kProbeHash ? a.colr : a.colp;
     const unsigned long long n_items = min(*a.n_items, a.items_cap);
     const int wmax = a.bitmap_bits / 32;
+    for (int i = threadIdx.x; i < a.u_ints; i += blockDim.x) U[i] = 0;
     if (threadIdx.x == 0) {
         const unsigned it = atomicAdd(a.queue, 1u);
         s_valid = it < n_items;
@@ -520,15 +544,11 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
                 tb.span = mx - mn + 1;
             }
         }
+        // the table region is all zeros here: every item resets what it set
         int nflush = 0;
         if (mode == kModeDirect) {
-            unsigned* cw = reinterpret_cast<unsigned*>(U);
             tb.cell = reinterpret_cast<unsigned short*>(U);
-            const int W = (tb.span + 1) >> 1;
-            for (int i = threadIdx.x; i < W; i += blockDim.x) cw[i] = 0u;
-            __syncthreads();
             for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell[L[lb + i] - tb.lo] = 1;
-            nflush = tb.span;
         } else if (mode == kModeBitmap) {
             const int W = (tb.span + 31) >> 5;
             unsigned* bits = reinterpret_cast<unsigned*>(U);
@@ -536,10 +556,6 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
             tb.bits = bits;
             tb.pre = pre;
             tb.cnts = U + wmax + (wmax + 1) / 2;
-            for (int i = threadIdx.x; i < W; i += blockDim.x) bits[i] = 0u;
-            if (PV)
-                for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cnts[i] = 0;
-            __syncthreads();
             for (int i = threadIdx.x; i < len; i += blockDim.x) {
                 const unsigned off = (unsigned)(L[lb + i] - tb.lo);
                 atomicOr(&bits[off >> 5], 1u << (off & 31u));
@@ -557,29 +573,19 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
                     run += __popc(bits[i]);
                 }
             }
-            nflush = W;
         } else if (mode == kModeHash) {
             int* keys = U;
             tb.keys = keys;
             tb.cnts = U + 4 * a.cap;
             tb.logS = max(5, 32 - __clz(4 * len - 1));  // load factor <= 1/4
-            const int S = 1 << tb.logS;
-            for (int i = threadIdx.x; i < S; i += blockDim.x) {
-                keys[i] = -1;
-                if (PV) tb.cnts[i] = 0;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < len; i += blockDim.x) table_insert(keys, tb.logS, L[lb + i]);
-            nflush = S;
+            for (int i = threadIdx.x; i < len; i += blockDim.x) table_insert_z(keys, tb.logS, L[lb + i]);
+            nflush = 1 << tb.logS;
         } else {
             int* keys = U;
             tb.keys = keys;
             tb.cnts = U + 4 * a.cap;
             tb.logS = 0;
-            for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                keys[i] = L[lb + i];
-                if (PV) tb.cnts[i] = 0;
-            }
+            for (int i = threadIdx.x; i < len; i += blockDim.x) keys[i] = L[lb + i];
             nflush = len;
         }
         __syncthreads();
@@ -591,32 +597,42 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
-        if (PV) {
-            if (mode == kModeDirect) {
-                for (int i = threadIdx.x; i < nflush; i += blockDim.x) {
-                    const int c = (int)tb.cell[i] - 1;
-                    if (c > 0) atomicAdd(&a.t[a.perm[tb.lo + i]], (unsigned long long)c);
+        // per-vertex counts of the table's keys, and reset of what this item set
+        if (mode == kModeDirect) {
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const int x = L[lb + i];
+                const int c = (int)tb.cell[x - tb.lo] - 1;
+                if (PV && c > 0) atomicAdd(&a.t[a.perm[x]], (unsigned long long)c);
+                tb.cell[x - tb.lo] = 0;
+            }
+        } else if (mode == kModeBitmap) {
+            if (PV) {
+                for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                    const int x = L[lb + i];
+                    const unsigned off = (unsigned)(x - tb.lo);
+                    const unsigned word = tb.bits[off >> 5];
+                    const int ord = (int)tb.pre[off >> 5] + __popc(word & ((1u << (off & 31u)) - 1u));
+                    const int c = tb.cnts[ord];
+                    if (c) atomicAdd(&a.t[a.perm[x]], (unsigned long long)c);
                 }
-            } else if (mode == kModeBitmap) {
-                for (int i = threadIdx.x; i < nflush; i += blockDim.x) {
-                    unsigned b = tb.bits[i];
-                    int ord = tb.pre[i];
-                    while (b) {
-                        const int bit = __ffs(b) - 1;
-                        const int c = tb.cnts[ord];
-                        if (c) atomicAdd(&a.t[a.perm[tb.lo + i * 32 + bit]], (unsigned long long)c);
-                        b &= b - 1u;
-                        ++ord;
-                    }
-                }
-            } else {
-                for (int i = threadIdx.x; i < nflush; i += blockDim.x) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cnts[i] = 0;
+                unsigned short* pre = const_cast<unsigned short*>(tb.pre);
+                for (int i = threadIdx.x; i < ((tb.span + 31) >> 5); i += blockDim.x) pre[i] = 0;
+            }
+            for (int i = threadIdx.x; i < len; i += blockDim.x)
+                const_cast<unsigned*>(tb.bits)[(unsigned)(L[lb + i] - tb.lo) >> 5] = 0u;
+        } else {
+            for (int i = threadIdx.x; i < nflush; i += blockDim.x) {
+                if (PV) {
                     const int c = tb.cnts[i];
                     if (c) {
-                        const int x = tb.keys[i];
+                        const int x = mode == kModeHash ? tb.keys[i] - 1 : tb.keys[i];
                         atomicAdd(&a.t[PROBE == kProbeHash ? a.perm[x] : x], (unsigned long long)c);
+                        tb.cnts[i] = 0;
                     }
                 }
+                if (mode == kModeHash) const_cast<int*>(tb.keys)[i] = 0;
             }
         }
         if (threadIdx.x == 0) {
