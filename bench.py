@@ -464,6 +464,24 @@ def run_serve(args, torch, binding, dev, rank, world):
     st = srv.stats()
     srv.close()
     lat = np.array(lat)
+    # saturated throughput with all slots against one slot, no resident graphs:
+    # the gain of overlapping requests on the device
+    def saturated(slots, k):
+        sv = binding.Server(device=dev.index, slots=slots, hbm_budget_bytes=40 << 30)
+        t0 = time.perf_counter()
+        tks = [(sv.submit(pool[picks[i]].n, pool[picks[i]].row_ptr, pool[picks[i]].col), pool[picks[i]].m)
+               for i in range(k)]
+        e = 0
+        for tk, m in tks:
+            r = sv.wait(tk, 600000)
+            assert r["status"] == 0
+            e += m
+        wall_s = time.perf_counter() - t0
+        sv.close()
+        return e / wall_s, k / wall_s
+    nsat = min(nreq, args.serve_seq_requests)
+    sat_many = saturated(args.slots, nsat)
+    sat_one = saturated(1, nsat)
     res = {
         "metric": "served count requests: edges/s, p50/p99 latency", "value": edges / wall, "unit": "edges/s",
         "n_gpus": world, "steps": nreq, "warmup": len(pool), "ms_per_step": wall * 1e3 / nreq,
@@ -473,6 +491,9 @@ def run_serve(args, torch, binding, dev, rank, world):
                                                     f"{args.slots} slots, cache={'on' if args.serve_cache else 'off'}"},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "closed_loop_capacity_rps": cap_rps, "server_stats": st,
+        "saturated": {"requests": nsat, "slots": args.slots, "edges_per_s": sat_many[0], "requests_per_s": sat_many[1],
+                      "one_slot_edges_per_s": sat_one[0], "one_slot_requests_per_s": sat_one[1],
+                      "gain": sat_many[0] / sat_one[0]},
     }
     return res, None
 
@@ -492,6 +513,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=0.0)
     ap.add_argument("--serve-cache", type=int, default=1)
+    ap.add_argument("--serve-seq-requests", type=int, default=500)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--rmat-scale", type=int, default=22, help="R-MAT scale of the rmat22 workload (small cases for profiling)")
     args = ap.parse_args()
