@@ -228,7 +228,10 @@ def oracle_rate(g, target_work=4e9, label=""):
 # ----------------------------------------------------------------------------- GPU arm
 def run_rmat_like(args, torch, binding, dev, rank, world):
     name = args.workload
-    g, desc = workload_graph(name, seed=rank, rmat_scale=args.rmat_scale)
+    shard = args.multi == "shard" and world > 1
+    # replicas: every rank counts its own graph (seed = rank); shard: all ranks
+    # count one graph (seed 0), each its part of the work, then one all-reduce
+    g, desc = workload_graph(name, seed=0 if shard else rank, rmat_scale=args.rmat_scale)
     log(f"[rank {rank}] {desc}: n={g.n} m={g.m}")
     B_alg, S, dplus, deg = algorithmic_bytes(g, per_vertex=True)
     ctx = binding.Context(dev.index)
@@ -240,7 +243,12 @@ def run_rmat_like(args, torch, binding, dev, rank, world):
 
     def step():
         o = ctx.build(g.n, rp, col, stream=stream)
-        ctx.count(o, total, pv, stream=stream)
+        if shard:
+            ctx.count_shard(o, rank, world, total, pv, stream=stream)
+            torch.distributed.all_reduce(total)
+            torch.distributed.all_reduce(pv)
+        else:
+            ctx.count(o, total, pv, stream=stream)
         o.release(stream)
 
     for _ in range(args.warmup):
@@ -312,7 +320,7 @@ def run_rmat_like(args, torch, binding, dev, rank, world):
     cta_ms = ph["count_cta"]
     achieved = cb["cta"] / (cta_ms * 1e-3) / 1e9 if cta_ms > 0 else None
     traffic = profiled_traffic(f"k_count_cta_{name}")
-    units = g.m * world
+    units = g.m * (1 if shard else world)
     res = {
         "metric": "edges/s (undirected input edges, build + count per step)",
         "value": units / (ms * 1e-3),
@@ -322,13 +330,15 @@ def run_rmat_like(args, torch, binding, dev, rank, world):
         "warmup": args.warmup,
         "ms_per_step": ms,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None,
         "dtype": "int32 ids / int64 counts",
         "data": "synthetic (seeded generator; the paper's SNAP/DIMACS graphs are not available)",
         "config": {"workload": desc, "n": g.n, "m_undirected": g.m, "per_vertex": True,
                    "l2": "no flush: input CSR %.0f MB > 129 MB L2" % ((8 * (g.n + 1) + 4 * g.nnz) / 1e6),
-                   "seed": rank, "parallelism": "replicas only (one graph per GPU)" if world > 1 else "1 GPU"},
+                   "seed": 0 if shard else rank,
+                   "parallelism": ("sharded count + all-reduce of (T, t)" if shard else
+                                   "replicas only (one graph per GPU)") if world > 1 else "1 GPU"},
         "triangles": T_gpu,
         "phases_ms": {k: round(v, 4) for k, v in ph.items() if v > 0},
         "build_ms": build_ms,
@@ -515,6 +525,8 @@ def main():
     ap.add_argument("--serve-cache", type=int, default=1)
     ap.add_argument("--serve-seq-requests", type=int, default=500)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--multi", default="replica", choices=["replica", "shard"],
+                    help="N>1: independent replicas (weak scaling) or one graph sharded over the GPUs (strong)")
     ap.add_argument("--rmat-scale", type=int, default=22, help="R-MAT scale of the rmat22 workload (small cases for profiling)")
     args = ap.parse_args()
     world, rank, local = dist_env()

@@ -147,6 +147,17 @@ tc_status tc_build_oriented_csr(tc_ctx* ctx, const tc_graph* g, tc_ocsr** out, v
  * Any number of tc_count calls may run on one tc_ocsr, on any streams. */
 tc_status tc_count(tc_ctx* ctx, const tc_ocsr* o, int64_t* total, int64_t* per_vertex, void* stream);
 
+/* One shard of tc_count, the building block of counting one graph on several
+ * GPUs (the paper counts on one GPU; each oriented edge is an independent unit
+ * of Sec. 3.2, so the work shards without changing the result).  Every GPU
+ * builds the same oriented CSR, shard s of nshards runs that equal part of
+ * the partition's work lists and source rows, and the caller sums `total`
+ * and `per_vertex` over the shards (an all-reduce): the sums equal tc_count's
+ * result exactly.  Outputs and synchronisation as in tc_count;
+ * TC_ERR_INVALID_ARG unless 0 <= shard < nshards. */
+tc_status tc_count_shard(tc_ctx* ctx, const tc_ocsr* o, int32_t shard, int32_t nshards, int64_t* total,
+                         int64_t* per_vertex, void* stream);
+
 /* Read-only view of a built oriented CSR (device pointers, owned by the handle). */
 typedef struct tc_ocsr_view {
     int64_t n;                 /* vertices */

@@ -87,6 +87,7 @@ _SIGS = {
     "tc_ctx_read_trace": (C.c_int, [_vp, _P(tc_trace)]),
     "tc_build_oriented_csr": (C.c_int, [_vp, _P(tc_graph), _P(_vp), _vp]),
     "tc_count": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "tc_count_shard": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     "tc_ocsr_get_view": (C.c_int, [_vp, _P(tc_ocsr_view)]),
     "tc_ocsr_copy": (C.c_int, [_vp, _vp, _vp, _vp]),
     "tc_ocsr_free": (None, [_vp]),
@@ -294,6 +295,12 @@ class Context:
     def count(self, o: OCSR, total=None, per_vertex=None, stream=None):
         """total / per_vertex: int64 torch tensors (device) or numpy arrays (host)."""
         _check(self, tc_count(self.handle, o.handle, _ptr(total), _ptr(per_vertex), _stream_ptr(stream)))
+        return total, per_vertex
+
+    def count_shard(self, o: OCSR, shard, nshards, total=None, per_vertex=None, stream=None):
+        """Partial counts of one shard; summed over all shards they equal count()."""
+        _check(self, tc_count_shard(self.handle, o.handle, int(shard), int(nshards), _ptr(total), _ptr(per_vertex),
+                                    _stream_ptr(stream)))
         return total, per_vertex
 
     def count_batch(self, vtx_off, edge_off, row_ptr, col, totals, per_vertex=None, stream=None, validate=False):

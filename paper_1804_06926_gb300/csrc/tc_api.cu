@@ -116,11 +116,11 @@ static cudaError_t upload(const T* h, int64_t count, T** d, cudaStream_t s) {
 // Count with outputs anywhere: device outputs are written in place; host
 // outputs go through device scratch, a copy back and a stream synchronise.
 static tc_status count_any(tc_ctx* ctx, const tc_ocsr* o, int64_t* totals, int64_t nt, int64_t* pv,
-                           cudaStream_t s) {
+                           cudaStream_t s, int shard = 0, int nshards = 1) {
     const bool h_tot = is_host_ptr(totals);
     const bool h_pv = pv && is_host_ptr(pv);
     if (!h_tot && !h_pv)
-        return count_device(ctx, o, (unsigned long long*)totals, (unsigned long long*)pv, s);
+        return count_device(ctx, o, (unsigned long long*)totals, (unsigned long long*)pv, s, shard, nshards);
     unsigned long long* dt = (unsigned long long*)totals;
     unsigned long long* dpv = (unsigned long long*)pv;
     cudaError_t e = cudaSuccess;
@@ -130,7 +130,7 @@ static tc_status count_any(tc_ctx* ctx, const tc_ocsr* o, int64_t* totals, int64
         if (h_tot) dev_free(dt, s);
         return set_err(ctx, TC_ERR_OOM, "count: output scratch allocation failed");
     }
-    tc_status st = count_device(ctx, o, dt, dpv, s);
+    tc_status st = count_device(ctx, o, dt, dpv, s, shard, nshards);
     if (st == TC_OK) {
         if (h_tot) cudaMemcpyAsync(totals, dt, sizeof(int64_t) * (size_t)nt, cudaMemcpyDeviceToHost, s);
         if (h_pv && o->n > 0) cudaMemcpyAsync(pv, dpv, sizeof(int64_t) * (size_t)o->n, cudaMemcpyDeviceToHost, s);
@@ -324,6 +324,16 @@ tc_status tc_count(tc_ctx* ctx, const tc_ocsr* o, int64_t* total, int64_t* per_v
     if (o->G > 0) return set_err(ctx, TC_ERR_INVALID_ARG, "batch handle: use tc_count_batch");
     cudaSetDevice(o->device);
     return count_any(ctx, o, total, 1, per_vertex, (cudaStream_t)stream);
+}
+
+tc_status tc_count_shard(tc_ctx* ctx, const tc_ocsr* o, int32_t shard, int32_t nshards, int64_t* total,
+                         int64_t* per_vertex, void* stream) {
+    if (!ctx || !o || !total) return set_err(ctx, TC_ERR_INVALID_ARG, "null argument");
+    if (nshards < 1 || shard < 0 || shard >= nshards)
+        return set_err(ctx, TC_ERR_INVALID_ARG, "shard must be in [0, nshards)");
+    if (o->G > 0) return set_err(ctx, TC_ERR_INVALID_ARG, "batch handle: use tc_count_batch");
+    cudaSetDevice(o->device);
+    return count_any(ctx, o, total, 1, per_vertex, (cudaStream_t)stream, shard, nshards);
 }
 
 tc_status tc_ocsr_get_view(const tc_ocsr* o, tc_ocsr_view* out) {

@@ -48,6 +48,7 @@ struct CountArgs {
     int direct_span;              // max span of a direct 16-bit cell table; 0 = off
     int u_ints;                   // ints of the table region of k_count_cta
     int64_t n;
+    int shard, nshards;           // this launch covers shard `shard` of `nshards` equal parts of the work
     int cap;                      // keys per table segment
     int small_max;
 };
@@ -487,11 +488,13 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
     // hash mode probes rank ids (so that a short span can use the bitmap);
     // the binary-search mode probes the id-sorted lists
     const int32_t* __restrict__ L = PROBE == kProbeHash ? a.colr : a.colp;
-    const unsigned long long n_items = min(*a.n_items, a.items_cap);
+    const unsigned long long n_all = min(*a.n_items, a.items_cap);
+    const unsigned long long it_lo = n_all * a.shard / a.nshards;
+    const unsigned long long n_items = n_all * (a.shard + 1) / a.nshards;
     const int wmax = a.bitmap_bits / 32;
     for (int i = threadIdx.x; i < a.u_ints; i += blockDim.x) U[i] = 0;
     if (threadIdx.x == 0) {
-        const unsigned it = atomicAdd(a.queue, 1u);
+        const unsigned long long it = it_lo + atomicAdd(a.queue, 1u);
         s_valid = it < n_items;
         if (s_valid) {
             s_cur = a.items[it];
@@ -506,11 +509,11 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
         const int p = item.p;
         const int64_t r0 = s_r0, r1 = s_r1;
         __syncthreads();  // everyone has read the current item
-        unsigned nit = 0;
+        unsigned long long nit = 0;
         Item nitem{};
         if (threadIdx.x == 0) {
             s_acc = 0;
-            nit = atomicAdd(a.queue, 1u);
+            nit = it_lo + atomicAdd(a.queue, 1u);
             if (nit < n_items) nitem = a.items[nit];
         }
         const int64_t lb = r0 + (int64_t)item.seg * a.cap;
@@ -661,10 +664,12 @@ __global__ void __launch_bounds__(256) k_count_warp(CountArgs a, int wcap) {
     const int per_warp = 8 * wcap;
     int* keys = smem + warp * per_warp;
     int* cnts = keys + 4 * wcap;
-    const unsigned long long n_items = min(*a.n_items, a.items_cap);
+    const unsigned long long n_all = min(*a.n_items, a.items_cap);
+    const unsigned long long it_lo = n_all * a.shard / a.nshards;
+    const unsigned long long n_items = n_all * (a.shard + 1) / a.nshards;
     for (;;) {
-        unsigned it = 0;
-        if (lane == 0) it = atomicAdd(a.queue, 1u);
+        unsigned long long it = 0;
+        if (lane == 0) it = it_lo + atomicAdd(a.queue, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
         const Item item = a.items[it];
@@ -719,7 +724,8 @@ __global__ void __launch_bounds__(256) k_count_small(CountArgs a) {
     __syncthreads();
     unsigned long long acc = 0;
     const int sm = a.small_max;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < a.n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u_lo = a.n * a.shard / a.nshards, u_hi = a.n * (a.shard + 1) / a.nshards;
+    for (int64_t u = u_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_hi; u += (int64_t)gridDim.x * blockDim.x) {
         const int du = a.dp[u];
         if (du < 2 || du > sm) continue;
         const int64_t ub = a.rpp[u];
@@ -812,7 +818,7 @@ static cudaError_t launch_tables(tc_ctx* ctx, const CountArgs& base, const tc_oc
 }
 
 tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals, unsigned long long* per_vertex,
-                       cudaStream_t s) {
+                       cudaStream_t s, int shard, int nshards) {
     const Tuning& tun = o->tun;
     const int64_t G = o->G > 0 ? o->G : 1;
     unsigned* queues = nullptr;
@@ -841,6 +847,8 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.n = o->n;
     a.cap = tun.table_cap;
     a.small_max = tun.small_max;
+    a.shard = shard;
+    a.nshards = nshards;
     a.colr = o->colr;
     a.perm = o->perm;
     a.rspan = o->rspan;

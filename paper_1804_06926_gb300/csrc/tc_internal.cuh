@@ -128,7 +128,8 @@ tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t npairs, const int32_t* sr
                        int64_t** row_ptr, int32_t** col, int64_t* nnz, cudaStream_t s);
 
 // Launch the count kernels.  totals: device int64 [G or 1], zeroed here.
+// shard/nshards: the launch covers that equal part of the work lists (0/1 = all).
 tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals,
-                       unsigned long long* per_vertex, cudaStream_t s);
+                       unsigned long long* per_vertex, cudaStream_t s, int shard = 0, int nshards = 1);
 
 }  // namespace tc
