@@ -147,6 +147,30 @@ tc_status tc_build_oriented_csr(tc_ctx* ctx, const tc_graph* g, tc_ocsr** out, v
  * Any number of tc_count calls may run on one tc_ocsr, on any streams. */
 tc_status tc_count(tc_ctx* ctx, const tc_ocsr* o, int64_t* total, int64_t* per_vertex, void* stream);
 
+/* Triangle-derived metrics, the use of the counts the paper names (Sec. 5,
+ * clustering coefficient and transitivity).  With d(v) the undirected degree:
+ *   wedges(v) = d(v)(d(v)-1)/2;  local[v] = t(v)/wedges(v), 0 when d(v) < 2;
+ *   *wedges = sum_v wedges(v);   *transitivity = 3T / *wedges, 0 without wedges.
+ * total and per_vertex are tc_count's device outputs for this handle;
+ * local (n doubles), transitivity and wedges may each be NULL, host or device
+ * memory.  Each ratio is one correctly rounded fp64 division of exact
+ * integers.  Synchronises `stream`.  Not available for batch handles. */
+tc_status tc_clustering(tc_ctx* ctx, const tc_ocsr* o, const int64_t* total, const int64_t* per_vertex, double* local,
+                        double* transitivity, int64_t* wedges, void* stream);
+
+/* Per-edge support and triangle listing (Sec. 1: enumerating the triangles
+ * is the subroutine of k-truss; every method the paper compares lists them).
+ * For every oriented edge (u, v) the sorted lists N+(u), N+(v) are merged;
+ * each common w gives the triangle (u, v, w), rank(u) < rank(v) < rank(w).
+ *   support    NULL or m int64: support[e] = triangles containing the edge
+ *              {u, col[e]} of the oriented CSR (the order of tc_ocsr_copy).
+ *   triangles  NULL or 3*capacity int32: the first `capacity` triangles found,
+ *              (u, v, w) vertex ids, in no particular order.
+ *   *count     the number of triangles (all of them, also beyond capacity).
+ * Outputs may be host or device memory; synchronises `stream`. */
+tc_status tc_edge_support(tc_ctx* ctx, const tc_ocsr* o, int64_t* support, int32_t* triangles, int64_t capacity,
+                          int64_t* count, void* stream);
+
 /* One shard of tc_count, the building block of counting one graph on several
  * GPUs (the paper counts on one GPU; each oriented edge is an independent unit
  * of Sec. 3.2, so the work shards without changing the result).  Every GPU

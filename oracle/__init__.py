@@ -57,6 +57,10 @@ def _load():
         lib.oracle_count.restype = _i64
         lib.oracle_vertex_triangles.argtypes = [_i64, _vp, _vp, _i64]
         lib.oracle_vertex_triangles.restype = _i64
+        lib.oracle_edge_support.argtypes = [_i64, _vp, _vp, _vp]
+        lib.oracle_edge_support.restype = None
+        lib.oracle_list_triangles.argtypes = [_i64, _vp, _vp, _vp, _i64]
+        lib.oracle_list_triangles.restype = _i64
         _lib = lib
     return _lib
 
@@ -120,3 +124,21 @@ def count_pairs(n: int, src, dst, per_vertex: bool = True):
 def vertex_triangles(n: int, row_ptr, col, v: int) -> int:
     rp, c = _c64(row_ptr), _c32(col)
     return int(_load().oracle_vertex_triangles(n, rp.ctypes.data, c.ctypes.data, int(v)))
+
+
+def edge_support(n: int, row_ptr, col) -> np.ndarray:
+    """Triangles containing each edge, per entry of the undirected CSR."""
+    rp, c = _c64(row_ptr), _c32(col)
+    sup = np.zeros(max(c.shape[0], 1), np.int64)
+    _load().oracle_edge_support(n, rp.ctypes.data, c.ctypes.data, sup.ctypes.data)
+    return sup[:c.shape[0]]
+
+
+def list_triangles(n: int, row_ptr, col) -> np.ndarray:
+    """All triangles as rows (u, v, w) in rank order (forward algorithm)."""
+    rpp, colp = orient(n, row_ptr, col)
+    T, _ = count_oriented(n, rpp, colp, per_vertex=False)
+    tri = np.zeros((max(T, 1), 3), np.int32)
+    got = _load().oracle_list_triangles(n, _c64(rpp).ctypes.data, _c32(colp).ctypes.data, tri.ctypes.data, T)
+    assert got == T
+    return tri[:T]

@@ -141,3 +141,49 @@ int64_t oracle_vertex_triangles(int64_t n, const int64_t* row_ptr, const int32_t
     }
     return twice / 2;
 }
+
+/* Per-edge support by definition: sup[e] = |N(a) & N(b)| for every entry
+ * e = (a, b) of the undirected CSR, the number of triangles containing the
+ * edge {a, b} (sorted merge of the two full neighbour lists). */
+void oracle_edge_support(int64_t n, const int64_t* row_ptr, const int32_t* col, int64_t* sup) {
+    for (int64_t a = 0; a < n; ++a) {
+        for (int64_t e = row_ptr[a]; e < row_ptr[a + 1]; ++e) {
+            int64_t b = col[e], c = 0;
+            int64_t i = row_ptr[a], iend = row_ptr[a + 1];
+            int64_t j = row_ptr[b], jend = row_ptr[b + 1];
+            while (i < iend && j < jend) {
+                if (col[i] < col[j]) ++i;
+                else if (col[i] > col[j]) ++j;
+                else { ++c; ++i; ++j; }
+            }
+            sup[e] = c;
+        }
+    }
+}
+
+/* Triangle listing with the forward algorithm: every triangle once as
+ * (u, v, w), u the lowest and w the highest rank.  Writes at most cap
+ * triples into tri[3*cap]; returns the number of triangles. */
+int64_t oracle_list_triangles(int64_t n, const int64_t* rpp, const int32_t* colp, int32_t* tri, int64_t cap) {
+    int64_t T = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        for (int64_t e = rpp[u]; e < rpp[u + 1]; ++e) {
+            int64_t v = colp[e];
+            int64_t i = rpp[u], iend = rpp[u + 1];
+            int64_t j = rpp[v], jend = rpp[v + 1];
+            while (i < iend && j < jend) {
+                if (colp[i] < colp[j]) ++i;
+                else if (colp[i] > colp[j]) ++j;
+                else {
+                    if (T < cap) {
+                        tri[3 * T] = (int32_t)u;
+                        tri[3 * T + 1] = (int32_t)v;
+                        tri[3 * T + 2] = colp[i];
+                    }
+                    ++T; ++i; ++j;
+                }
+            }
+        }
+    }
+    return T;
+}

@@ -88,6 +88,8 @@ _SIGS = {
     "tc_build_oriented_csr": (C.c_int, [_vp, _P(tc_graph), _P(_vp), _vp]),
     "tc_count": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "tc_count_shard": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
+    "tc_clustering": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tc_edge_support": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
     "tc_ocsr_get_view": (C.c_int, [_vp, _P(tc_ocsr_view)]),
     "tc_ocsr_copy": (C.c_int, [_vp, _vp, _vp, _vp]),
     "tc_ocsr_free": (None, [_vp]),
@@ -302,6 +304,22 @@ class Context:
         _check(self, tc_count_shard(self.handle, o.handle, int(shard), int(nshards), _ptr(total), _ptr(per_vertex),
                                     _stream_ptr(stream)))
         return total, per_vertex
+
+    def clustering(self, o: OCSR, total, per_vertex, local=None, stream=None):
+        """(transitivity, wedges); fills `local` (n doubles) when given."""
+        tr = C.c_double(0.0)
+        w = C.c_int64(0)
+        _check(self, tc_clustering(self.handle, o.handle, _ptr(total), _ptr(per_vertex), _ptr(local),
+                                   C.addressof(tr), C.addressof(w), _stream_ptr(stream)))
+        return tr.value, w.value
+
+    def edge_support(self, o: OCSR, support=None, triangles=None, stream=None) -> int:
+        """Number of triangles; fills support (m int64) and up to len(triangles) // 3 triples."""
+        cnt = C.c_int64(0)
+        cap = 0 if triangles is None else int(triangles.shape[0]) // 3
+        _check(self, tc_edge_support(self.handle, o.handle, _ptr(support), _ptr(triangles), cap, C.addressof(cnt),
+                                     _stream_ptr(stream)))
+        return cnt.value
 
     def count_batch(self, vtx_off, edge_off, row_ptr, col, totals, per_vertex=None, stream=None, validate=False):
         b = tc_batch()

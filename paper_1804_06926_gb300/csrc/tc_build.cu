@@ -574,15 +574,16 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     A((void**)&o->items_cta, sizeof(Item) * o->items_cta_cap);
     A((void**)&o->dc, sizeof(DevCounters));
     if (batch) A((void**)&o->row_graph, sizeof(int32_t) * std::max<int64_t>(n, 1));
-    A((void**)&deg, sizeof(int32_t) * std::max<int64_t>(n, 1));
+    A((void**)&o->deg, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&pc, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A(&scan_tmp, stb);
     if (e != cudaSuccess) {
         tc_ocsr_free(o);
-        dev_free(deg, s); dev_free(pc, s); dev_free(scan_tmp, s);
+        dev_free(pc, s); dev_free(scan_tmp, s);
         return set_err(ctx, TC_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
-    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 5 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
+    deg = o->deg;
+    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 6 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
                          + (batch ? sizeof(int32_t) * n : 0));
     cudaMemsetAsync(o->dc, 0, sizeof(DevCounters), s);
 
@@ -608,7 +609,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         cudaMemcpyAsync(&herr, &o->dc->error, sizeof(int), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess || herr != 0) {
-            dev_free(deg, s); dev_free(pc, s); dev_free(scan_tmp, s);
+            dev_free(pc, s); dev_free(scan_tmp, s);
             tc_ocsr_free(o);
             if (e != cudaSuccess) return cuda_err(ctx, e, "validate");
             return set_err(ctx, TC_ERR_INVALID_GRAPH, "input is not a simple symmetric sorted CSR (code " + std::to_string(herr) + ")");
@@ -633,7 +634,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         dev_free(ka, s);
         dev_free(kb, s);
         if (e != cudaSuccess) {
-            dev_free(deg, s); dev_free(pc, s); dev_free(scan_tmp, s);
+            dev_free(pc, s); dev_free(scan_tmp, s);
             tc_ocsr_free(o);
             return set_err(ctx, TC_ERR_OOM, "rank: device allocation failed");
         }
@@ -650,7 +651,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     if (e == cudaSuccess) e = dev_alloc((void**)&nbc, sizeof(unsigned long long), s);
     if (e != cudaSuccess) {
         dev_free(bchunks, s); dev_free(bcnt, s); dev_free(nbc, s);
-        dev_free(deg, s); dev_free(pc, s); dev_free(scan_tmp, s);
+        dev_free(pc, s); dev_free(scan_tmp, s);
         tc_ocsr_free(o);
         return set_err(ctx, TC_ERR_OOM, "orient: device allocation failed");
     }
@@ -709,7 +710,6 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
                                                      o->items_warp, o->items_warp_cap, o->items_cta, o->items_cta_cap, o->dc);
         TC_LAUNCH(ctx);
     }
-    dev_free(deg, s);
     dev_free(pc, s);
     dev_free(scan_tmp, s);
     e = cudaGetLastError();

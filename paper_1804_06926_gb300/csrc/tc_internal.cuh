@@ -50,6 +50,7 @@ struct tc_ocsr {
     int64_t* rpp = nullptr;     // [n+1] oriented row offsets
     int32_t* colp = nullptr;    // [m]
     int32_t* dplus = nullptr;   // [n] out-degrees
+    int32_t* deg = nullptr;     // [n] undirected degrees
     int32_t* rank = nullptr;    // [n] position of each vertex in (degree, id) order
     int32_t* perm = nullptr;    // [n] inverse of rank
     int32_t* colr = nullptr;    // [m] colp relabelled to rank ids (same row layout)
