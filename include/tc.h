@@ -171,6 +171,14 @@ tc_status tc_clustering(tc_ctx* ctx, const tc_ocsr* o, const int64_t* total, con
 tc_status tc_edge_support(tc_ctx* ctx, const tc_ocsr* o, int64_t* support, int32_t* triangles, int64_t capacity,
                           int64_t* count, void* stream);
 
+/* Alg. 3 (Sec. 3.3) as the masked sparse product the paper proposes as future
+ * work (Sec. 5: upper triangle only, only where A is nonzero, B = LU never
+ * written).  With vertices in decreasing rank order, the upper-triangle entry
+ * of C = A o (LU) at the oriented edge e = (u, v) is |N+(u) & N+(v)|; c[e]
+ * receives it for every oriented edge (m int64, the order of tc_ocsr_copy)
+ * and *total (nullable) their sum, T.  Host or device outputs; synchronises. */
+tc_status tc_masked_product(tc_ctx* ctx, const tc_ocsr* o, int64_t* c, int64_t* total, void* stream);
+
 /* One shard of tc_count, the building block of counting one graph on several
  * GPUs (the paper counts on one GPU; each oriented edge is an independent unit
  * of Sec. 3.2, so the work shards without changing the result).  Every GPU

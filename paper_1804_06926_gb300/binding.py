@@ -90,6 +90,7 @@ _SIGS = {
     "tc_count_shard": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     "tc_clustering": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tc_edge_support": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
+    "tc_masked_product": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "tc_ocsr_get_view": (C.c_int, [_vp, _P(tc_ocsr_view)]),
     "tc_ocsr_copy": (C.c_int, [_vp, _vp, _vp, _vp]),
     "tc_ocsr_free": (None, [_vp]),
@@ -320,6 +321,12 @@ class Context:
         _check(self, tc_edge_support(self.handle, o.handle, _ptr(support), _ptr(triangles), cap, C.addressof(cnt),
                                      _stream_ptr(stream)))
         return cnt.value
+
+    def masked_product(self, o: OCSR, c, stream=None) -> int:
+        """Per-edge entries of the masked product C = A o (LU) (Alg. 3); returns their sum T."""
+        tot = C.c_int64(0)
+        _check(self, tc_masked_product(self.handle, o.handle, _ptr(c), C.addressof(tot), _stream_ptr(stream)))
+        return tot.value
 
     def count_batch(self, vtx_off, edge_off, row_ptr, col, totals, per_vertex=None, stream=None, validate=False):
         b = tc_batch()

@@ -15,7 +15,9 @@
 
 namespace tc {
 
-template <bool SUP, bool LIST>
+// SUP: support of all three edges; LIST: write the triangles; LOWER: only the
+// per-edge count c(u, v) = |N+(u) & N+(v)| into sup[e] (the masked product).
+template <bool SUP, bool LIST, bool LOWER = false>
 __global__ void __launch_bounds__(256) k_support_list(int64_t n, const int64_t* __restrict__ rpp,
                                                       const int32_t* __restrict__ colp,
                                                       unsigned long long* __restrict__ sup, int32_t* __restrict__ tri,
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(256) k_support_list(int64_t n, const int64_t* 
                 }
             }
             if (SUP && c) atomicAdd(&sup[e], c);
+            if (LOWER) sup[e] = c;
             found += c;
         }
     }
@@ -114,5 +117,45 @@ extern "C" tc_status tc_edge_support(tc_ctx* ctx, const tc_ocsr* o, int64_t* sup
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "edge support");
+    return TC_OK;
+}
+
+// Alg. 3 of the paper (Sec. 3.3) with the TC-specific masking it proposes as
+// future work (Sec. 5: compute only the upper triangle, only where A is
+// nonzero, and never write B = LU to memory): with the vertices in decreasing
+// rank order, C = A o (LU) is nonzero only at edges, and for the oriented
+// edge e = (u, v) its upper-triangle entry is |N+(u) & N+(v)|.  c[e] receives
+// it for every oriented edge (order of tc_ocsr_copy); sum c = T.
+extern "C" tc_status tc_masked_product(tc_ctx* ctx, const tc_ocsr* o, int64_t* c, int64_t* total, void* stream) {
+    if (!ctx || !o || !c) return set_err(ctx, TC_ERR_INVALID_ARG, "masked product: c is required");
+    if (o->G > 0) return set_err(ctx, TC_ERR_INVALID_ARG, "masked product: batch handles are not supported");
+    cudaSetDevice(o->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaPointerAttributes at;
+    const bool h_c = cudaPointerGetAttributes(&at, c) != cudaSuccess || at.type == cudaMemoryTypeHost ||
+                     at.type == cudaMemoryTypeUnregistered;
+    cudaGetLastError();
+    unsigned long long* dc = (unsigned long long*)c;
+    unsigned long long* dcount = nullptr;
+    cudaError_t e = dev_alloc((void**)&dcount, sizeof(unsigned long long), s);
+    if (e == cudaSuccess && h_c) e = dev_alloc((void**)&dc, sizeof(int64_t) * (size_t)std::max<int64_t>(o->m, 1), s);
+    if (e != cudaSuccess) {
+        dev_free(dcount, s);
+        return set_err(ctx, TC_ERR_OOM, "masked product: scratch allocation failed");
+    }
+    cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s);
+    const unsigned grid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((o->n * 32 + 255) / 256, (int64_t)ctx->num_sms * 16));
+    if (o->n > 0) {
+        k_support_list<false, false, true><<<grid, 256, 0, s>>>(o->n, o->rpp, o->colp, dc, nullptr, 0, dcount);
+        TC_LAUNCH(ctx);
+    }
+    if (h_c && o->m > 0) cudaMemcpyAsync(c, dc, sizeof(int64_t) * (size_t)o->m, cudaMemcpyDeviceToHost, s);
+    if (total) cudaMemcpyAsync(total, dcount, sizeof(int64_t), cudaMemcpyDefault, s);
+    if (h_c) dev_free(dc, s);
+    dev_free(dcount, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "masked product");
     return TC_OK;
 }

@@ -52,3 +52,28 @@ def test_support_and_listing(B, g):
     assert all(tuple(t) in wanted for t in small.reshape(-1, 3).tolist()[:min(T, small.shape[0] // 3)])
     assert ctx.edge_support(o) == T
     o.free()
+
+
+def test_masked_product_matches_dense_alg3(B):
+    """c[e] equals Fig. 3's C = A o (LU) at that edge when the rows are ordered
+    by decreasing rank (dense Alg. 3 oracle, no nnz permutation of its own)."""
+    from oracle import dense
+    ctx = B.Context(0)
+    for g in (gen.er(300, 2000, seed=4), gen.rmat(8, 8, seed=6), gen.ba(250, 5, seed=1)):
+        o = ctx.build(g.n, torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+        rpp, colp = o.copy_to_host()
+        c = np.zeros(max(colp.shape[0], 1), np.int64)
+        T = ctx.masked_product(o, c)
+        o.free()
+        deg = np.diff(g.row_ptr)
+        order = np.lexsort((np.arange(g.n), deg))[::-1]          # decreasing (d, id)
+        pos = np.empty(g.n, np.int64)
+        pos[order] = np.arange(g.n)
+        A = np.zeros((g.n, g.n), np.int64)
+        u = np.repeat(np.arange(g.n), deg)
+        A[pos[u], pos[g.col]] = 1
+        _, _, _, _, Cm, T3 = dense.alg3_matrices(A, permute=False)
+        assert T == T3 == oracle.count(g.n, g.row_ptr, g.col)[0]
+        uo = np.repeat(np.arange(g.n), np.diff(rpp))
+        lo, hi = np.minimum(pos[uo], pos[colp]), np.maximum(pos[uo], pos[colp])
+        np.testing.assert_array_equal(c[:colp.shape[0]], Cm[lo, hi])
