@@ -179,6 +179,16 @@ tc_status tc_edge_support(tc_ctx* ctx, const tc_ocsr* o, int64_t* support, int32
  * and *total (nullable) their sum, T.  Host or device outputs; synchronises. */
 tc_status tc_masked_product(tc_ctx* ctx, const tc_ocsr* o, int64_t* c, int64_t* total, void* stream);
 
+/* Subgraph matching of a labelled triangle (Alg. 1, Sec. 3.1): the number of
+ * triangles whose three vertex labels are the multiset {query[0..2]}.
+ * g is a device CSR (as in tc_graph, TC_IN_HOST not accepted), labels[n] device
+ * int32, query[3] host int32, total host or device.  Candidate edges (label
+ * pair of a query edge) are filtered on the device, then joined by the
+ * set-intersection count; for a query {a, a, b} the {a, a, a} triangles of
+ * the a-a subgraph are subtracted.  Synchronises `stream`. */
+tc_status tc_count_labelled(tc_ctx* ctx, const tc_graph* g, const int32_t* labels, const int32_t* query,
+                            int64_t* total, void* stream);
+
 /* One shard of tc_count, the building block of counting one graph on several
  * GPUs (the paper counts on one GPU; each oriented edge is an independent unit
  * of Sec. 3.2, so the work shards without changing the result).  Every GPU

@@ -142,3 +142,13 @@ def list_triangles(n: int, row_ptr, col) -> np.ndarray:
     got = _load().oracle_list_triangles(n, _c64(rpp).ctypes.data, _c32(colp).ctypes.data, tri.ctypes.data, T)
     assert got == T
     return tri[:T]
+
+
+def count_labelled(n: int, row_ptr, col, labels, query) -> int:
+    """Triangles whose label multiset is `query`: list every triangle, check its labels."""
+    tri = list_triangles(n, row_ptr, col)
+    if tri.shape[0] == 0:
+        return 0
+    lab = np.asarray(labels)[tri]
+    lab.sort(axis=1)
+    return int((lab == np.sort(np.asarray(query))).all(axis=1).sum())

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build", platform.machine())
 LIB = os.path.join(HERE, "libtc.so")
 STAMP = LIB + ".arch"
-SOURCES = ["tc_build.cu", "tc_count.cu", "tc_sort.cu", "tc_api.cu", "tc_serve.cu", "tc_noalloc.cu", "tc_metrics.cu", "tc_support.cu"]
+SOURCES = ["tc_build.cu", "tc_count.cu", "tc_sort.cu", "tc_api.cu", "tc_serve.cu", "tc_noalloc.cu", "tc_metrics.cu", "tc_support.cu", "tc_labels.cu"]
 HEADERS = [os.path.join(CSRC, "tc_internal.cuh"), os.path.join(ROOT, "include", "tc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

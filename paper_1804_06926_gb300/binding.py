@@ -91,6 +91,7 @@ _SIGS = {
     "tc_clustering": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tc_edge_support": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
     "tc_masked_product": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "tc_count_labelled": (C.c_int, [_vp, _P(tc_graph), _vp, _vp, _vp, _vp]),
     "tc_ocsr_get_view": (C.c_int, [_vp, _P(tc_ocsr_view)]),
     "tc_ocsr_copy": (C.c_int, [_vp, _vp, _vp, _vp]),
     "tc_ocsr_free": (None, [_vp]),
@@ -326,6 +327,17 @@ class Context:
         """Per-edge entries of the masked product C = A o (LU) (Alg. 3); returns their sum T."""
         tot = C.c_int64(0)
         _check(self, tc_masked_product(self.handle, o.handle, _ptr(c), C.addressof(tot), _stream_ptr(stream)))
+        return tot.value
+
+    def count_labelled(self, n, row_ptr, col, labels, query, stream=None) -> int:
+        """Triangles whose vertex labels are the multiset `query` (device CSR and labels)."""
+        g = tc_graph()
+        g.n, g.nnz = int(n), int(col.shape[0])
+        g.row_ptr, g.col = _ptr(row_ptr), _ptr(col)
+        q = (C.c_int32 * 3)(*[int(x) for x in query])
+        tot = C.c_int64(0)
+        _check(self, tc_count_labelled(self.handle, C.byref(g), _ptr(labels), q, C.addressof(tot),
+                                       _stream_ptr(stream)))
         return tot.value
 
     def count_batch(self, vtx_off, edge_off, row_ptr, col, totals, per_vertex=None, stream=None, validate=False):
