@@ -15,8 +15,6 @@ namespace tc {
 // ============================================================================
 // Device-wide exclusive scan (reduce-then-scan over 2048-element tiles)
 // ============================================================================
-constexpr int kBigRow = 4096;     // rows longer than this are oriented chunk by chunk
-constexpr int kBigChunk = 8192;   // entries per chunk of a long row
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -148,13 +146,6 @@ __global__ void k_rank_from_sorted(int64_t n, const unsigned long long* __restri
     }
 }
 
-// colr[e] = rank[colp[e]]: the oriented lists renamed to rank ids
-__global__ void k_relabel(int64_t m, const int32_t* __restrict__ colp, const int32_t* __restrict__ rank,
-                          int32_t* __restrict__ colr) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
-        colr[e] = rank[colp[e]];
-}
-
 // ============================================================================
 // validation of a CSR input (TC_VALIDATE): ids in range, rows strictly
 // ascending (sorted, no duplicates), no self-loops, symmetric.
@@ -194,168 +185,266 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ r
 }
 
 // ============================================================================
-// a-2 / a-3  orientation filter and compaction.
-// A group of GS lanes walks one row; neighbour v is kept iff
-// rank(u) < rank(v), rank = (d, id).  The count pass writes d+(u); the
-// scatter pass writes the kept neighbours at rpp[u] in their input order, so
-// rows stay ascending.
+// Merge-path tiles over a CSR (rows i, entries j).  The merged sequence of the
+// n row ends and the nnz entries is cut into tiles of kMpTile items, so every
+// tile carries the same work whatever the degrees: a tile of one hub row and
+// a tile of a thousand one-entry rows cost the same.  Boundary t of the cut is
+// the coordinate (i, j) = (rows ended, entries consumed) on diagonal
+// t * kMpTile, found by binary search (a row end is taken before an entry
+// with the same offset).
 // ============================================================================
-template <int GS>
-__device__ __forceinline__ unsigned group_mask() {
-    if constexpr (GS == 32) {
-        return 0xffffffffu;
-    } else {
-        const int g = (threadIdx.x & 31) / GS;
-        return ((1u << GS) - 1u) << (g * GS);
+constexpr int kMpThreads = 256;
+constexpr int kMpIpt = 8;
+constexpr int kMpTile = kMpThreads * kMpIpt;
+
+int64_t mp_tiles(int64_t n, int64_t nnz) { return (n + nnz + kMpTile - 1) / kMpTile; }
+
+__global__ void k_mp_coords(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, int64_t ntiles,
+                            longlong2* __restrict__ coord) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = min(t * (int64_t)kMpTile, n + nnz);
+        int64_t lo = max((int64_t)0, d - nnz), hi = min(d, n);
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (rp[mid + 1] <= d - 1 - mid) lo = mid + 1;
+            else hi = mid;
+        }
+        coord[t] = make_longlong2(lo, d - lo);
     }
 }
 
-template <int GS, bool SCATTER, bool BATCH>
-__global__ void __launch_bounds__(256) k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
-                                                const int64_t* __restrict__ vtx_off, int32_t* __restrict__ cnt,
-                                                const int64_t* __restrict__ rpp, int32_t* __restrict__ colp,
-                                                const int32_t* __restrict__ rank, int32_t* __restrict__ colr,
-                                                int2* __restrict__ rspan) {
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % GS;
-    const int shift = (lane / GS) * GS;
-    const unsigned gm = group_mask<GS>();
-    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / GS;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS; u < n; u += ngroups) {
-        const int64_t b = rp[u], e = rp[u + 1];
-        const int du = (int)(e - b);
-        if (du > kBigRow) {  // long rows are cut into chunks for k_orient_big
-            if (!SCATTER && sub == 0) {
-                cnt[u] = 0;
-                rspan[u] = make_int2(0x7fffffff, -1);
-            }
-            continue;
-        }
-        const int64_t base = BATCH ? vtx_off[row_graph[u]] : 0;
-        int kept = 0;
-        int64_t out = 0;
-        int rmin = 0x7fffffff, rmax = -1;
-        if (SCATTER) out = rpp[u];
-        for (int64_t j0 = b; j0 < e; j0 += GS) {
-            const int64_t i = j0 + sub;
-            const bool valid = i < e;
-            const int64_t v = valid ? (int64_t)col[i] + base : 0;
-            const int dv = valid ? deg[v] : 0;
-            const bool keep = valid && (du < dv || (du == dv && u < v));
-            const unsigned bal = __ballot_sync(gm, keep);
-            const unsigned mine = (GS == 32) ? bal : ((bal >> shift) & ((1u << (GS & 31)) - 1u));
-            if (SCATTER && keep) {
-                const int64_t pos = out + kept + __popc(mine & ((1u << sub) - 1u));
-                const int r = rank[v];
-                colp[pos] = (int32_t)v;
-                colr[pos] = r;
-                rmin = min(rmin, r);
-                rmax = max(rmax, r);
-            }
-            kept += __popc(mine);
-        }
-        if (!SCATTER && sub == 0) cnt[u] = kept;
-        if (SCATTER) {  // span of the row in rank ids
-#pragma unroll
-            for (int o = GS / 2; o; o >>= 1) {
-                rmin = min(rmin, __shfl_xor_sync(gm, rmin, o));
-                rmax = max(rmax, __shfl_xor_sync(gm, rmax, o));
-            }
-            if (sub == 0) rspan[u] = make_int2(rmin, rmax);
-        }
-    }
-}
-
-// Rows longer than kBigRow are cut into chunks of kBigChunk entries, each
-// handled by one CTA, so that hub rows do not serialise on one warp.  The
-// count pass sums each chunk's kept entries; the scatter pass places a
-// chunk's kept entries after those of the row's earlier chunks.
-struct BigChunk {
-    int u, j, first, pad;
+// Shared state of one tile: local rows i0 .. i0+nr-1 and entries j0 .. j0+ne-1.
+template <bool BATCH>
+struct MpTile {
+    int cs[kMpTile + 2];                        // row starts relative to j0, clamped to [0, ne]
+    int du[kMpTile + 1];                        // full length of each local row
+    int base[BATCH ? kMpTile + 1 : 1];          // batch: first global id of the row's graph
+    __align__(16) unsigned short row[kMpTile];  // local row of each entry
+    int wmax[kMpThreads / 32];
+    long long i0, j0;
+    int nr, ne, nend;                           // rows whose end lies in the tile: the first nend
+    int first_full;                             // local row 0 starts at j0 (it is not a continuation)
 };
 
-__global__ void k_big_chunks(int64_t n, const int64_t* __restrict__ rp, BigChunk* __restrict__ chunks,
-                             int64_t cap, unsigned long long* __restrict__ n_chunks) {
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t d = rp[u + 1] - rp[u];
-        if (d <= kBigRow) continue;
-        const int nch = (int)((d + kBigChunk - 1) / kBigChunk);
-        const unsigned long long first = atomicAdd(n_chunks, (unsigned long long)nch);
-        for (int j = 0; j < nch; ++j)
-            if ((int64_t)(first + j) < cap) chunks[first + j] = BigChunk{(int)u, j, (int)first, 0};
+// Fill S for tile t.  Ends with a barrier.
+template <bool BATCH>
+__device__ void mp_tile(MpTile<BATCH>& S, int64_t t, int64_t n, const longlong2* __restrict__ coord,
+                        const int64_t* __restrict__ rp, const int32_t* __restrict__ row_graph,
+                        const int64_t* __restrict__ vtx_off) {
+    const longlong2 c0 = coord[t], c1 = coord[t + 1];
+    const int64_t i0 = c0.x, j0 = c0.y;
+    const int ne = (int)(c1.y - j0);
+    const int nr = (int)max((int64_t)0, min((int64_t)c1.x, n - 1) - i0 + 1);
+    for (int k = threadIdx.x; k <= nr; k += blockDim.x) {
+        const int64_t s = rp[i0 + k];
+        S.cs[k] = (int)min(max(s - j0, (int64_t)0), (int64_t)ne);
+        if (k < nr) {
+            S.du[k] = (int)(rp[i0 + k + 1] - s);
+            if (BATCH) S.base[k] = (int)vtx_off[row_graph[i0 + k]];
+        }
+    }
+    reinterpret_cast<uint4*>(S.row)[threadIdx.x] = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x == 0) {
+        S.i0 = i0;
+        S.j0 = j0;
+        S.nr = nr;
+        S.ne = ne;
+        S.nend = (int)(c1.x - i0);
+        S.first_full = nr > 0 && rp[i0] == j0;
+    }
+    __syncthreads();
+    // every row with entries here marks its first one; a running maximum then
+    // gives each entry its row (rows with entries have distinct starts)
+    for (int k = 1 + threadIdx.x; k < nr; k += blockDim.x)
+        if (S.cs[k] < S.cs[k + 1]) S.row[S.cs[k]] = (unsigned short)k;
+    __syncthreads();
+    uint4 pk = reinterpret_cast<uint4*>(S.row)[threadIdx.x];
+    unsigned short* v = reinterpret_cast<unsigned short*>(&pk);
+    int run = 0;
+#pragma unroll
+    for (int q = 0; q < kMpIpt; ++q) {
+        run = max(run, (int)v[q]);
+        v[q] = (unsigned short)run;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = max(inc, y);
+    }
+    if (lane == 31) S.wmax[w] = inc;
+    int before = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) before = 0;
+    __syncthreads();
+    for (int k = 0; k < w; ++k) before = max(before, S.wmax[k]);
+#pragma unroll
+    for (int q = 0; q < kMpIpt; ++q) v[q] = (unsigned short)max(before, (int)v[q]);
+    reinterpret_cast<uint4*>(S.row)[threadIdx.x] = pk;
+    __syncthreads();
+}
+
+// OR the ballot of 32 consecutive entries starting at global index g into a bitmask.
+__device__ __forceinline__ void or_bits(unsigned* __restrict__ mask, int64_t g, unsigned bal) {
+    if (!bal) return;
+    const int64_t w = g >> 5;
+    const int sh = (int)(g & 31);
+    atomicOr(&mask[w], bal << sh);
+    if (sh) {
+        const unsigned hi = bal >> (32 - sh);
+        if (hi) atomicOr(&mask[w + 1], hi);
     }
 }
 
-template <bool SCATTER, bool BATCH>
-__global__ void __launch_bounds__(256) k_orient_big(const BigChunk* __restrict__ chunks,
-                                                    const unsigned long long* __restrict__ n_chunks, int64_t cap,
-                                                    const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                    const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
-                                                    const int64_t* __restrict__ vtx_off, int32_t* __restrict__ cnt,
-                                                    int32_t* __restrict__ chunk_cnt, const int64_t* __restrict__ rpp,
-                                                    int32_t* __restrict__ colp, const int32_t* __restrict__ rank,
-                                                    int32_t* __restrict__ colr, int2* __restrict__ rspan) {
-    __shared__ int s_w[8];
-    __shared__ long long s_off;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t nc = (int64_t)min(*n_chunks, (unsigned long long)cap);
-    for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
-        const BigChunk ch = chunks[c];
-        const int64_t u = ch.u;
-        const int64_t rb = rp[u], re = rp[u + 1];
-        const int du = (int)(re - rb);
-        const int64_t b = rb + (int64_t)ch.j * kBigChunk, e = min(re, b + kBigChunk);
-        const int64_t base = BATCH ? vtx_off[row_graph[u]] : 0;
-        if (SCATTER && threadIdx.x == 0) {
-            long long off = rpp[u];
-            for (int64_t k = ch.first; k < c; ++k) off += chunk_cnt[k];
-            s_off = off;
+// number of set bits of mask before global index g (pre = exclusive prefix of word popcounts)
+__device__ __forceinline__ int64_t bits_before(const unsigned* __restrict__ mask, const int64_t* __restrict__ pre, int64_t g) {
+    const int64_t w = g >> 5;
+    return pre[w] + __popc(mask[w] & ((1u << (g & 31)) - 1u));
+}
+
+__global__ void k_popc(const unsigned* __restrict__ mask, int64_t nw, int32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __popc(mask[i]);
+}
+
+// ============================================================================
+// a-2 / a-3  orientation filter and compaction (Sec. 4.2.1).
+// Entry (u, v) is kept iff rank(u) < rank(v), rank = (d, id).  Pass 1 sets
+// one bit per kept entry.  Kept entries keep their input order, so the
+// position of a kept entry in the oriented CSR is the number of kept entries
+// before it (a prefix count over the bitmask) and rpp[u] is that count at
+// row_ptr[u]; pass 2 scatters the kept neighbours (vertex and rank ids) and
+// records each row's smallest and largest rank id.
+// ============================================================================
+template <bool BATCH>
+__global__ void __launch_bounds__(kMpThreads) k_orient_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
+                                                             const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                             const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
+                                                             const int64_t* __restrict__ vtx_off, unsigned* __restrict__ keep,
+                                                             int2* __restrict__ rspan) {
+    __shared__ MpTile<BATCH> S;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        mp_tile<BATCH>(S, t, n, coord, rp, row_graph, vtx_off);
+        const int64_t i0 = S.i0, j0 = S.j0;
+        const int ne = S.ne, nr = S.nr;
+        // rows that continue into another tile collect their rank span with
+        // atomics in pass 2; start them empty here
+        if (threadIdx.x == 0 && nr > 0 && (!S.first_full || S.nend == 0)) rspan[i0] = make_int2(0x7fffffff, -1);
+        if (threadIdx.x == 1 && nr > 0 && nr - 1 >= S.nend) rspan[i0 + nr - 1] = make_int2(0x7fffffff, -1);
+        // all loads of the tile first (8 independent streams, then 8 gathers)
+        int32_t vv[kMpIpt];
+        int dv[kMpIpt];
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int e = q * kMpThreads + threadIdx.x;
+            vv[q] = e < ne ? col[j0 + e] + (BATCH ? S.base[S.row[e]] : 0) : 0;
         }
-        int run = 0;
-        int rmin = 0x7fffffff, rmax = -1;
-        for (int64_t r0 = b; r0 < e; r0 += blockDim.x) {
-            const int64_t i = r0 + threadIdx.x;
-            const bool valid = i < e;
-            const int64_t v = valid ? (int64_t)col[i] + base : 0;
-            const int dv = valid ? deg[v] : 0;
-            const bool keep = valid && (du < dv || (du == dv && u < v));
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) s_w[w] = __popc(bal);
-            __syncthreads();
-            int before = 0, tot = 0;
-            for (int k = 0; k < nw; ++k) {
-                const int c2 = s_w[k];
-                if (k < w) before += c2;
-                tot += c2;
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) dv[q] = q * kMpThreads + (int)threadIdx.x < ne ? deg[vv[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int e = q * kMpThreads + threadIdx.x;
+            bool kp = false;
+            if (e < ne) {
+                const int k = S.row[e];
+                const int du = S.du[k];
+                kp = du < dv[q] || (du == dv[q] && i0 + k < (int64_t)vv[q]);
             }
-            if (SCATTER && keep) {
-                const int64_t pos = s_off + run + before + __popc(bal & ((1u << lane) - 1u));
-                const int r = rank[v];
-                colp[pos] = (int32_t)v;
-                colr[pos] = r;
-                rmin = min(rmin, r);
-                rmax = max(rmax, r);
-            }
-            run += tot;
-            __syncthreads();
-        }
-        if (SCATTER) {
-            for (int o = 16; o; o >>= 1) {
-                rmin = min(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-                rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-            }
-            if (lane == 0 && rmax >= 0) {
-                atomicMin(&rspan[u].x, rmin);
-                atomicMax(&rspan[u].y, rmax);
-            }
-        }
-        if (!SCATTER && threadIdx.x == 0) {
-            chunk_cnt[c] = run;
-            if (run) atomicAdd(&cnt[u], run);
+            const unsigned bal = __ballot_sync(0xffffffffu, kp);
+            if (lane == 0) or_bits(keep, j0 + q * kMpThreads + w * 32, bal);
         }
         __syncthreads();
     }
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kMpThreads) k_orient_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
+                                                               const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                               const int32_t* __restrict__ rank, const int32_t* __restrict__ row_graph,
+                                                               const int64_t* __restrict__ vtx_off, const unsigned* __restrict__ keep,
+                                                               const int64_t* __restrict__ kpre, int64_t* __restrict__ rpp,
+                                                               int32_t* __restrict__ colp, int32_t* __restrict__ colr,
+                                                               int2* __restrict__ rspan) {
+    __shared__ MpTile<BATCH> S;
+    __shared__ int s_mn[kMpTile + 1], s_mx[kMpTile + 1];
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) rpp[0] = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int k = threadIdx.x; k <= kMpTile; k += blockDim.x) {
+            s_mn[k] = 0x7fffffff;
+            s_mx[k] = -1;
+        }
+        mp_tile<BATCH>(S, t, n, coord, rp, row_graph, vtx_off);
+        const int64_t i0 = S.i0, j0 = S.j0;
+        const int ne = S.ne, nr = S.nr;
+        // all loads of the tile first: keep words and lists, then the rank gathers
+        unsigned kw[kMpIpt];
+        int32_t vv[kMpIpt];
+        int rr[kMpIpt];
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int e = q * kMpThreads + threadIdx.x;
+            kw[q] = 0;
+            vv[q] = 0;
+            if (e < ne) {
+                const int64_t g = j0 + e;
+                kw[q] = (keep[g >> 5] >> (g & 31)) & 1u;
+                vv[q] = col[g] + (BATCH ? S.base[S.row[e]] : 0);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) rr[q] = kw[q] ? rank[vv[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int e = q * kMpThreads + threadIdx.x;
+            const bool valid = e < ne;
+            int k = 0xffff, mn = 0x7fffffff, mx = -1;
+            if (valid) {
+                k = S.row[e];
+                if (kw[q]) {
+                    const int64_t g = j0 + e;
+                    const int64_t pos = bits_before(keep, kpre, g);
+                    colp[pos] = vv[q];
+                    colr[pos] = rr[q];
+                    mn = mx = rr[q];
+                }
+            }
+            // segmented min / max over runs of equal rows within the warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int k2 = __shfl_down_sync(0xffffffffu, k, o);
+                const int mn2 = __shfl_down_sync(0xffffffffu, mn, o);
+                const int mx2 = __shfl_down_sync(0xffffffffu, mx, o);
+                if (lane + o < 32 && k2 == k) {
+                    mn = min(mn, mn2);
+                    mx = max(mx, mx2);
+                }
+            }
+            const int kprev = __shfl_up_sync(0xffffffffu, k, 1);
+            if (valid && (lane == 0 || kprev != k) && mx >= 0) {
+                atomicMin(&s_mn[k], mn);
+                atomicMax(&s_mx[k], mx);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+            const int64_t u = i0 + k;
+            if (k < S.nend) rpp[u + 1] = bits_before(keep, kpre, j0 + S.cs[k + 1]);
+            if (k < S.nend && (k > 0 || S.first_full)) {
+                rspan[u] = make_int2(s_mn[k], s_mx[k]);
+            } else if (s_mx[k] >= 0) {
+                atomicMin(&rspan[u].x, s_mn[k]);
+                atomicMax(&rspan[u].y, s_mx[k]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_dplus(int64_t n, const int64_t* __restrict__ rpp, int32_t* __restrict__ dplus) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        dplus[u] = (int32_t)(rpp[u + 1] - rpp[u]);
 }
 
 // ============================================================================
@@ -368,6 +457,13 @@ __global__ void __launch_bounds__(256) k_orient_big(const BigChunk* __restrict__
 //           shared-memory table and the partner's (shorter) list is streamed
 //           against it: the "small x large" kernel the paper proposes in its
 //           Sec. 5 discussion, applied to every non-small edge.
+// The partners of pivot p are stored at pcol[prp[p] .. prp[p+1]): first the
+// U-part, the entries of p's own row with p as pivot, in row order; then the
+// V-part, the rows u whose entry (u, p) made p the pivot.  With
+//   U(x)    = number of U-part entries of the oriented CSR before entry x,
+//   nV(p)   = size of p's V-part, Vpre(p) = sum of nV(q) over q < p,
+// prp[p] = U(rpp[p]) + Vpre(p), a U-part entry x of row u lands at
+// U(x) + Vpre(u), and the V-part of p fills the slots just below prp[p+1].
 // ============================================================================
 enum { kSkip = 0, kSmall = 1, kPivot = 2 };
 
@@ -377,62 +473,102 @@ __device__ __forceinline__ int edge_class(int a, int b, int small_max) {
     return kPivot;
 }
 
-template <int GS, bool SCATTER>
-__global__ void __launch_bounds__(256) k_pivot(int64_t n, const int64_t* __restrict__ rpp, const int32_t* __restrict__ colp,
-                                               const int32_t* __restrict__ dp, int small_max,
-                                               int32_t* __restrict__ pc, const int64_t* __restrict__ prp,
-                                               int32_t* __restrict__ pcol, DevCounters* __restrict__ dc) {
+__global__ void __launch_bounds__(kMpThreads) k_pivot_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
+                                                            const int64_t* __restrict__ rpp, const int32_t* __restrict__ colp,
+                                                            const int32_t* __restrict__ dp, int small_max,
+                                                            unsigned* __restrict__ umask, unsigned* __restrict__ vmask,
+                                                            int32_t* __restrict__ nv, DevCounters* __restrict__ dc) {
+    __shared__ MpTile<false> S;
     __shared__ unsigned long long s_piv, s_small;
-    if (!SCATTER && threadIdx.x == 0) { s_piv = 0; s_small = 0; }
-    if (!SCATTER) __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % GS;
-    const int shift = (lane / GS) * GS;
-    const unsigned gm = group_mask<GS>();
-    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / GS;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) { s_piv = 0; s_small = 0; }
     unsigned long long my_piv = 0, my_small = 0;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS; u < n; u += ngroups) {
-        const int a = dp[u];
-        if (a <= 1) continue;  // uniform within the group
-        const int64_t b0 = rpp[u], e = rpp[u + 1];
-        for (int64_t j0 = b0; j0 < e; j0 += GS) {
-            const int64_t i = j0 + sub;
-            const bool valid = i < e;
-            const int v = valid ? colp[i] : 0;
-            const int b = valid ? dp[v] : 0;
-            const int cls = valid ? edge_class(a, b, small_max) : kSkip;
-            const bool piv_u = cls == kPivot && a >= b;
-            const bool piv_v = cls == kPivot && a < b;
-            const unsigned bu = __ballot_sync(gm, piv_u);
-            const unsigned mine = (GS == 32) ? bu : ((bu >> shift) & ((1u << (GS & 31)) - 1u));
-            const int nu = __popc(mine);
-            const int leader = __ffs(mine) - 1;  // lane within group
-            if (!SCATTER) {
-                if (piv_u && sub == leader) atomicAdd(&pc[u], nu);
-                if (piv_v) atomicAdd(&pc[v], 1);
-                my_piv += piv_u + piv_v;
-                my_small += cls == kSmall;
-            } else {
-                int basepos = 0;
-                if (piv_u && sub == leader) basepos = atomicAdd(&pc[u], nu);
-                basepos = __shfl_sync(gm, basepos, shift + (leader < 0 ? 0 : leader));
-                if (piv_u) pcol[prp[u] + basepos + __popc(mine & ((1u << sub) - 1u))] = v;
-                if (piv_v) pcol[prp[v] + atomicAdd(&pc[v], 1)] = (int32_t)u;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        mp_tile<false>(S, t, n, coord, rpp, nullptr, nullptr);
+        const int64_t j0 = S.j0;
+        const int ne = S.ne;
+        int av[kMpIpt], vv[kMpIpt], bv[kMpIpt];
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int e = q * kMpThreads + threadIdx.x;
+            av[q] = e < ne ? S.du[S.row[e]] : 0;
+            vv[q] = av[q] > 1 ? colp[j0 + e] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) bv[q] = av[q] > 1 ? dp[vv[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int cls = edge_class(av[q], bv[q], small_max);
+            const bool pu = cls == kPivot && av[q] >= bv[q];
+            const bool pv = cls == kPivot && av[q] < bv[q];
+            my_small += cls == kSmall;
+            if (pv) atomicAdd(&nv[vv[q]], 1);
+            my_piv += pu + pv;
+            const unsigned bu = __ballot_sync(0xffffffffu, pu), bw = __ballot_sync(0xffffffffu, pv);
+            if (lane == 0) {
+                const int64_t g = j0 + q * kMpThreads + w * 32;
+                or_bits(umask, g, bu);
+                or_bits(vmask, g, bw);
             }
         }
-    }
-    if (!SCATTER) {
-        // block-aggregate the class counters
-        for (int o = 16; o; o >>= 1) {
-            my_piv += __shfl_xor_sync(0xffffffffu, my_piv, o);
-            my_small += __shfl_xor_sync(0xffffffffu, my_small, o);
-        }
-        if (lane == 0) { atomicAdd(&s_piv, my_piv); atomicAdd(&s_small, my_small); }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            atomicAdd(&dc->n_pivot_edges, s_piv);
-            atomicAdd(&dc->n_small_edges, s_small);
+    }
+    for (int o = 16; o; o >>= 1) {
+        my_piv += __shfl_xor_sync(0xffffffffu, my_piv, o);
+        my_small += __shfl_xor_sync(0xffffffffu, my_small, o);
+    }
+    if (lane == 0) { atomicAdd(&s_piv, my_piv); atomicAdd(&s_small, my_small); }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&dc->n_pivot_edges, s_piv);
+        atomicAdd(&dc->n_small_edges, s_small);
+    }
+}
+
+// prp[p] = U(rpp[p]) + Vpre(p), p = 0 .. n
+__global__ void k_pivot_offsets(int64_t n, const int64_t* __restrict__ rpp, const unsigned* __restrict__ umask,
+                                const int64_t* __restrict__ upre, const int64_t* __restrict__ vpre,
+                                int64_t* __restrict__ prp) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += (int64_t)gridDim.x * blockDim.x)
+        prp[p] = bits_before(umask, upre, rpp[p]) + vpre[p];
+}
+
+// nv[p] counts down from nV(p) while p's V-part is filled.
+__global__ void __launch_bounds__(kMpThreads) k_pivot_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
+                                                              const int64_t* __restrict__ rpp, const int32_t* __restrict__ colp,
+                                                              const unsigned* __restrict__ umask, const unsigned* __restrict__ vmask,
+                                                              const int64_t* __restrict__ upre, const int64_t* __restrict__ vpre,
+                                                              const int64_t* __restrict__ prp, int32_t* __restrict__ nv,
+                                                              int32_t* __restrict__ pcol) {
+    __shared__ MpTile<false> S;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        mp_tile<false>(S, t, n, coord, rpp, nullptr, nullptr);
+        const int64_t i0 = S.i0, j0 = S.j0;
+        const int ne = S.ne;
+        unsigned uw[kMpIpt], vw[kMpIpt];
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int e = q * kMpThreads + threadIdx.x;
+            uw[q] = vw[q] = 0;
+            if (e < ne) {
+                const int64_t g = j0 + e;
+                uw[q] = umask[g >> 5];
+                vw[q] = vmask[g >> 5];
+            }
         }
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int e = q * kMpThreads + threadIdx.x;
+            const int64_t g = j0 + e;
+            const int bit = (int)(g & 31);
+            const bool pu = (uw[q] >> bit) & 1u, pv = (vw[q] >> bit) & 1u;
+            if (!pu && !pv) continue;
+            const int64_t u = i0 + S.row[e];
+            const int32_t v = colp[g];
+            if (pu) pcol[upre[g >> 5] + __popc(uw[q] & ((1u << bit) - 1u)) + vpre[u]] = v;
+            else pcol[prp[(int64_t)v + 1] - atomicSub(&nv[v], 1)] = (int32_t)u;
+        }
+        __syncthreads();
     }
 }
 
@@ -480,46 +616,10 @@ __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restr
 // ============================================================================
 // host side
 // ============================================================================
-static int pick_group(int64_t n, int64_t entries, const char* env_name) {
-    if (const char* v = std::getenv(env_name)) {  // tuning override: 4, 8, 16 or 32 lanes per row
-        const int g = std::atoi(v);
-        if (g == 4 || g == 8 || g == 16 || g == 32) return g;
-    }
-    double avg = n > 0 ? (double)entries / (double)n : 0.0;
-    if (avg <= 4.0) return 4;
-    if (avg <= 8.0) return 8;
-    if (avg <= 16.0) return 16;
-    return 32;
-}
-
 static unsigned grid_for(int64_t work, int threads, int num_sms, int per_sm = 8) {
     int64_t want = (work + threads - 1) / threads;
     int64_t cap = (int64_t)num_sms * per_sm;
     return (unsigned)std::max<int64_t>(1, std::min(want, cap));
-}
-
-template <bool SCATTER, bool BATCH>
-static void launch_orient(int gs, unsigned grid, cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* col,
-                          const int32_t* deg, const int32_t* rg, const int64_t* vo, int32_t* cnt, const int64_t* rpp,
-                          int32_t* colp, const int32_t* rank, int32_t* colr, int2* rspan) {
-    switch (gs) {
-        case 4: k_orient<4, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp, rank, colr, rspan); break;
-        case 8: k_orient<8, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp, rank, colr, rspan); break;
-        case 16: k_orient<16, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp, rank, colr, rspan); break;
-        default: k_orient<32, SCATTER, BATCH><<<grid, 256, 0, s>>>(n, rp, col, deg, rg, vo, cnt, rpp, colp, rank, colr, rspan); break;
-    }
-}
-
-template <bool SCATTER>
-static void launch_pivot(int gs, unsigned grid, cudaStream_t s, int64_t n, const int64_t* rpp, const int32_t* colp,
-                         const int32_t* dp, int small_max, int32_t* pc, const int64_t* prp, int32_t* pcol,
-                         DevCounters* dc) {
-    switch (gs) {
-        case 4: k_pivot<4, SCATTER><<<grid, 256, 0, s>>>(n, rpp, colp, dp, small_max, pc, prp, pcol, dc); break;
-        case 8: k_pivot<8, SCATTER><<<grid, 256, 0, s>>>(n, rpp, colp, dp, small_max, pc, prp, pcol, dc); break;
-        case 16: k_pivot<16, SCATTER><<<grid, 256, 0, s>>>(n, rpp, colp, dp, small_max, pc, prp, pcol, dc); break;
-        default: k_pivot<32, SCATTER><<<grid, 256, 0, s>>>(n, rpp, colp, dp, small_max, pc, prp, pcol, dc); break;
-    }
 }
 
 static int64_t isqrt_bound(int64_t x) {
@@ -554,8 +654,6 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
 
     int32_t* deg = nullptr;
     int32_t* pc = nullptr;
-    void* scan_tmp = nullptr;
-    const size_t stb = scan_tmp_bytes(n);
     cudaError_t e = cudaSuccess;
     auto A = [&](void** p, size_t b) {
         if (e == cudaSuccess) e = dev_alloc(p, std::max<size_t>(b, 16), s);
@@ -576,10 +674,9 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     if (batch) A((void**)&o->row_graph, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->deg, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&pc, sizeof(int32_t) * std::max<int64_t>(n, 1));
-    A(&scan_tmp, stb);
     if (e != cudaSuccess) {
         tc_ocsr_free(o);
-        dev_free(pc, s); dev_free(scan_tmp, s);
+        dev_free(pc, s);
         return set_err(ctx, TC_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
     deg = o->deg;
@@ -609,7 +706,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         cudaMemcpyAsync(&herr, &o->dc->error, sizeof(int), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess || herr != 0) {
-            dev_free(pc, s); dev_free(scan_tmp, s);
+            dev_free(pc, s);
             tc_ocsr_free(o);
             if (e != cudaSuccess) return cuda_err(ctx, e, "validate");
             return set_err(ctx, TC_ERR_INVALID_GRAPH, "input is not a simple symmetric sorted CSR (code " + std::to_string(herr) + ")");
@@ -634,76 +731,103 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         dev_free(ka, s);
         dev_free(kb, s);
         if (e != cudaSuccess) {
-            dev_free(pc, s); dev_free(scan_tmp, s);
+            dev_free(pc, s);
             tc_ocsr_free(o);
             return set_err(ctx, TC_ERR_OOM, "rank: device allocation failed");
         }
     }
-    const int gs = pick_group(n, nnz, "TC_ORIENT_GROUP");
-    const unsigned og = grid_for(n * gs, 256, ns, 16);
-    // long rows: chunk list (bounded by nnz/kBigChunk + nnz/kBigRow)
-    const int64_t bc_cap = nnz / kBigChunk + nnz / kBigRow + 2;
-    BigChunk* bchunks = nullptr;
-    int32_t* bcnt = nullptr;
-    unsigned long long* nbc = nullptr;
-    e = dev_alloc((void**)&bchunks, sizeof(BigChunk) * bc_cap, s);
-    if (e == cudaSuccess) e = dev_alloc((void**)&bcnt, sizeof(int32_t) * bc_cap, s);
-    if (e == cudaSuccess) e = dev_alloc((void**)&nbc, sizeof(unsigned long long), s);
+    // merge-path tiles: nt1 over the input CSR, nt2 over the oriented CSR
+    const int64_t nt1 = mp_tiles(n, nnz), nt2 = mp_tiles(n, m);
+    const int64_t kw = (nnz >> 5) + 1, uw = (m >> 5) + 1;  // bitmask words (one spare: prefix at the end)
+    longlong2* coord = nullptr;
+    unsigned *keep = nullptr, *umask = nullptr, *vmask = nullptr;
+    int32_t* wpc = nullptr;
+    int64_t *kpre = nullptr, *upre = nullptr, *vpre = nullptr;
+    void* wtmp = nullptr;
+    const size_t wtb = scan_tmp_bytes(std::max(kw, std::max(uw, n)));
+    auto B = [&](void** p, size_t b) {
+        if (e == cudaSuccess) e = dev_alloc(p, std::max<size_t>(b, 16), s);
+    };
+    B((void**)&coord, sizeof(longlong2) * (std::max(nt1, nt2) + 1));
+    B((void**)&keep, sizeof(unsigned) * kw);
+    B((void**)&umask, sizeof(unsigned) * uw);
+    B((void**)&vmask, sizeof(unsigned) * uw);
+    B((void**)&wpc, sizeof(int32_t) * std::max(kw, uw));
+    B((void**)&kpre, sizeof(int64_t) * (kw + 1));
+    B((void**)&upre, sizeof(int64_t) * (uw + 1));
+    B((void**)&vpre, sizeof(int64_t) * n1);
+    B(&wtmp, wtb);
+    auto free_tmp = [&]() {
+        dev_free(coord, s); dev_free(keep, s); dev_free(umask, s); dev_free(vmask, s); dev_free(wpc, s);
+        dev_free(kpre, s); dev_free(upre, s); dev_free(vpre, s); dev_free(wtmp, s);
+        dev_free(pc, s);
+    };
     if (e != cudaSuccess) {
-        dev_free(bchunks, s); dev_free(bcnt, s); dev_free(nbc, s);
-        dev_free(pc, s); dev_free(scan_tmp, s);
+        free_tmp();
         tc_ocsr_free(o);
         return set_err(ctx, TC_ERR_OOM, "orient: device allocation failed");
     }
-    const unsigned bg = (unsigned)std::max(1, ns * 4);
-    // a-2: kept count per row = d+(u)
+    const int per_sm = 8;
+    const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nt1, (int64_t)ns * per_sm));
+    const unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nt2, (int64_t)ns * per_sm));
+    // a-2: one bit per kept entry
     {
         PhaseScope ph(ctx, kPhOrientCount, s);
-        cudaMemsetAsync(nbc, 0, sizeof(unsigned long long), s);
-        if (n > 0) k_big_chunks<<<grid_for(n, 256, ns), 256, 0, s>>>(n, row_ptr, bchunks, bc_cap, nbc);
-        if (batch) launch_orient<false, true>(gs, og, s, n, row_ptr, col, deg, o->row_graph, vtx_off, o->dplus, nullptr, nullptr, nullptr, nullptr, o->rspan);
-        else launch_orient<false, false>(gs, og, s, n, row_ptr, col, deg, nullptr, nullptr, o->dplus, nullptr, nullptr, nullptr, nullptr, o->rspan);
-        if (batch) k_orient_big<false, true><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, o->row_graph, vtx_off, o->dplus, bcnt, nullptr, nullptr, nullptr, nullptr, nullptr);
-        else k_orient_big<false, false><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, nullptr, nullptr, o->dplus, bcnt, nullptr, nullptr, nullptr, nullptr, nullptr);
-        ctx->launches += 3;
+        cudaMemsetAsync(keep, 0, sizeof(unsigned) * kw, s);
+        k_mp_coords<<<grid_for(nt1 + 1, 256, ns), 256, 0, s>>>(n, nnz, row_ptr, nt1, coord);
+        if (nt1 > 0) {
+            if (batch) k_orient_flags<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, o->row_graph, vtx_off, keep, o->rspan);
+            else k_orient_flags<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, nullptr, nullptr, keep, o->rspan);
+        }
+        ctx->launches += 2;
     }
-    // a-3: row offsets of the oriented CSR, then the stable scatter
+    // a-3: prefix counts over the bitmask give every kept entry its place
     {
         PhaseScope ph(ctx, kPhOrientScan, s);
-        scan_i32_to_i64(o->dplus, o->rpp, n, scan_tmp, stb, s);
-        ctx->launches += 3;
+        k_popc<<<grid_for(kw, 256, ns), 256, 0, s>>>(keep, kw, wpc);
+        scan_i32_to_i64(wpc, kpre, kw, wtmp, wtb, s);
+        ctx->launches += 4;
     }
     {
         PhaseScope ph(ctx, kPhOrientScatter, s);
-        if (batch) launch_orient<true, true>(gs, og, s, n, row_ptr, col, deg, o->row_graph, vtx_off, nullptr, o->rpp, o->colp, o->rank, o->colr, o->rspan);
-        else launch_orient<true, false>(gs, og, s, n, row_ptr, col, deg, nullptr, nullptr, nullptr, o->rpp, o->colp, o->rank, o->colr, o->rspan);
-        if (batch) k_orient_big<true, true><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, o->row_graph, vtx_off, nullptr, bcnt, o->rpp, o->colp, o->rank, o->colr, o->rspan);
-        else k_orient_big<true, false><<<bg, 256, 0, s>>>(bchunks, nbc, bc_cap, row_ptr, col, deg, nullptr, nullptr, nullptr, bcnt, o->rpp, o->colp, o->rank, o->colr, o->rspan);
-        ctx->launches += 2;
+        cudaMemsetAsync(o->rpp, 0, sizeof(int64_t), s);
+        if (nt1 > 0) {
+            if (batch) k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
+            else k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
+            TC_LAUNCH(ctx);
+        }
+        if (n > 0) {
+            k_dplus<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->rpp, o->dplus);
+            TC_LAUNCH(ctx);
+        }
     }
-    dev_free(bchunks, s);
-    dev_free(bcnt, s);
-    dev_free(nbc, s);
-    // a-4: classify, group oriented edges by pivot, cut work items
-    const int gs2 = pick_group(n, m, "TC_PIVOT_GROUP");
-    const unsigned pg = grid_for(n * gs2, 256, ns, 16);
+    // a-4: classify, group oriented edges by pivot
     {
         PhaseScope ph(ctx, kPhPivotCount, s);
         cudaMemsetAsync(pc, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), s);
-        launch_pivot<false>(gs2, pg, s, n, o->rpp, o->colp, o->dplus, tun.small_max, pc, nullptr, nullptr, o->dc);
-        TC_LAUNCH(ctx);
+        cudaMemsetAsync(umask, 0, sizeof(unsigned) * uw, s);
+        cudaMemsetAsync(vmask, 0, sizeof(unsigned) * uw, s);
+        k_mp_coords<<<grid_for(nt2 + 1, 256, ns), 256, 0, s>>>(n, m, o->rpp, nt2, coord);
+        if (nt2 > 0) k_pivot_flags<<<g2, kMpThreads, 0, s>>>(n, nt2, coord, o->rpp, o->colp, o->dplus, tun.small_max, umask, vmask, pc, o->dc);
+        ctx->launches += 2;
     }
     {
         PhaseScope ph(ctx, kPhPivotScan, s);
-        scan_i32_to_i64(pc, o->prp, n, scan_tmp, stb, s);
-        ctx->launches += 3;
+        k_popc<<<grid_for(uw, 256, ns), 256, 0, s>>>(umask, uw, wpc);
+        scan_i32_to_i64(wpc, upre, uw, wtmp, wtb, s);
+        scan_i32_to_i64(pc, vpre, n, wtmp, wtb, s);
+        k_pivot_offsets<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, o->rpp, umask, upre, vpre, o->prp);
+        ctx->launches += 8;
     }
     {
         PhaseScope ph(ctx, kPhPivotScatter, s);
-        cudaMemsetAsync(pc, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), s);
-        launch_pivot<true>(gs2, pg, s, n, o->rpp, o->colp, o->dplus, tun.small_max, pc, o->prp, o->pcol, o->dc);
-        TC_LAUNCH(ctx);
+        if (nt2 > 0) {
+            k_pivot_scatter<<<g2, kMpThreads, 0, s>>>(n, nt2, coord, o->rpp, o->colp, umask, vmask, upre, vpre, o->prp, pc, o->pcol);
+            TC_LAUNCH(ctx);
+        }
     }
+    dev_free(coord, s); dev_free(keep, s); dev_free(umask, s); dev_free(vmask, s); dev_free(wpc, s);
+    dev_free(kpre, s); dev_free(upre, s); dev_free(vpre, s); dev_free(wtmp, s);
     if (n > 0) {
         PhaseScope ph(ctx, kPhItems, s);
         k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->dplus, o->prp, tun.warp_max, tun.table_cap, tun.chunk,
@@ -711,7 +835,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         TC_LAUNCH(ctx);
     }
     dev_free(pc, s);
-    dev_free(scan_tmp, s);
+   
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         tc_ocsr_free(o);
