@@ -198,7 +198,7 @@ def profiled_traffic(kernel_tag):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_rate(g, target_work=4e9, label=""):
+def oracle_rate(g, target_work=4e9, label="", all_cores=None):
     """Time the CPU oracle on a bounded sample: orientation of the full graph,
     then the forward count over every k-th source row; extrapolate to the whole
     graph by merge work.  Returns (edges/s, description, seconds)."""
@@ -222,7 +222,43 @@ def oracle_rate(g, target_work=4e9, label=""):
     desc = (f"{label}oracle orientation of the full graph ({t_orient:.2f} s) + forward count over every "
             f"{stride}th source row ({100 * frac:.1f}% of the merge work, {t_sample:.2f} s), "
             f"extrapolated by merge work to {t_full:.1f} s for the whole graph; 1 thread")
+    if all_cores is not None:
+        all_cores.update(oracle_rate_all_cores(g, rpp, colp, stride, frac, t_orient))
     return g.m / t_full, desc, t_orient + t_sample
+
+
+def _oracle_rows(args):
+    """Pool worker: the oracle's forward count over rows start, start+step, ..."""
+    import oracle
+    path, n, start, step = args
+    d = np.load(path)
+    return oracle.count_rows(n, d["rpp"], d["colp"], start, n, step)
+
+
+def _noop(_):
+    return 0
+
+
+def oracle_rate_all_cores(g, rpp, colp, stride, frac, t_orient):
+    """The same sample as oracle_rate, its rows split over every host core
+    (spawn-started worker processes, each running the oracle unchanged on an
+    interleaved share); the orientation stays one call of the oracle on one
+    core."""
+    import multiprocessing as mp
+    import tempfile
+    procs = max(1, os.cpu_count() or 1)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "ocsr.npz")
+        np.savez(path, rpp=rpp, colp=colp)
+        with mp.get_context("spawn").Pool(procs) as pool:
+            pool.map(_noop, range(procs))
+            t1 = time.perf_counter()
+            pool.map(_oracle_rows, [(path, g.n, j * stride, stride * procs) for j in range(procs)])
+            t_par = time.perf_counter() - t1
+    t_full = t_orient + (t_par / frac if frac > 0 else 0.0)
+    return {"value": g.m / t_full, "unit": "edges/s", "cores": procs, "kind": "oracle",
+            "sample": f"the same rows as the 1-thread sample over {procs} worker processes ({t_par:.2f} s), "
+                      f"orientation on one core ({t_orient:.2f} s), extrapolated to {t_full:.1f} s"}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -572,8 +608,10 @@ def main():
         res, g = run_rmat_like(args, torch, binding, dev, rank, world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and g is not None:
-        v, d, _ = oracle_rate(g)
-        res["cpu_baseline"] = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": d}
+        allc = {}
+        v, d, _ = oracle_rate(g, all_cores=allc)
+        res["cpu_baseline"] = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": d,
+                               "all_cores": allc}
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
