@@ -223,7 +223,10 @@ def oracle_rate(g, target_work=4e9, label="", all_cores=None):
             f"{stride}th source row ({100 * frac:.1f}% of the merge work, {t_sample:.2f} s), "
             f"extrapolated by merge work to {t_full:.1f} s for the whole graph; 1 thread")
     if all_cores is not None:
-        all_cores.update(oracle_rate_all_cores(g, rpp, colp, stride, frac, t_orient))
+        if t_sample >= 1.0:
+            all_cores.update(oracle_rate_all_cores(g, rpp, colp, stride, frac, t_orient))
+        else:  # worker start-up would dominate a sample this small
+            all_cores.update({"value": None, "sample": f"not split: the 1-thread sample took {t_sample:.2f} s"})
     return g.m / t_full, desc, t_orient + t_sample
 
 
