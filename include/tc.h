@@ -91,8 +91,9 @@ typedef struct tc_config {
     int32_t bitmap_bits;   /* CTA items whose pivot list spans at most this many rank ids (vertices
                               renamed in (degree, id) order) probe a shared-memory bitmap instead of
                               the hash table; multiple of 32, <= 262144; default 131072; -1 = never */
-    int32_t direct_span;   /* ... and those spanning at most this many rank ids one 16-bit counter cell
-                              per rank id (presence and hits in one probe); <= 16384; default 16384;
+    int32_t direct_span;   /* ... and those spanning at most this many rank ids one counter cell per
+                              rank id (presence and hits in one probe; 32-bit cells up to half this
+                              span, 16-bit above); <= 16384; default 16384;
                               -1 = never (needs bitmap_bits > 0) */
     int32_t reserved[8];
 } tc_config;

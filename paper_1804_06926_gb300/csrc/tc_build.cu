@@ -313,8 +313,10 @@ __global__ void k_popc(const unsigned* __restrict__ mask, int64_t nw, int32_t* _
 // one bit per kept entry.  Kept entries keep their input order, so the
 // position of a kept entry in the oriented CSR is the number of kept entries
 // before it (a prefix count over the bitmask) and rpp[u] is that count at
-// row_ptr[u]; pass 2 scatters the kept neighbours (vertex and rank ids) and
-// records each row's smallest and largest rank id.
+// row_ptr[u] (k_rows).  Pass 2 scatters the kept neighbours: vertex ids to
+// colp, rank ids to colr, whose rows start at multiples of 4 (rp4) and are
+// padded with -1 so that the count kernels read them as whole aligned 16-byte
+// vectors; it also records each row's smallest and largest rank id.
 // ============================================================================
 template <bool BATCH>
 __global__ void __launch_bounds__(kMpThreads) k_orient_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
@@ -358,18 +360,33 @@ __global__ void __launch_bounds__(kMpThreads) k_orient_flags(int64_t n, int64_t 
     }
 }
 
+// rpp[u] = kept entries before row u; d+(u); the padded length of u's colr row
+__global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned* __restrict__ keep,
+                       const int64_t* __restrict__ kpre, int64_t* __restrict__ rpp, int32_t* __restrict__ dplus,
+                       int32_t* __restrict__ pad4) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = bits_before(keep, kpre, rp[u]);
+        rpp[u] = s;
+        if (u < n) {
+            const int d = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
+            dplus[u] = d;
+            pad4[u] = (d + 3) & ~3;
+        }
+    }
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(kMpThreads) k_orient_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                                const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                                const int32_t* __restrict__ rank, const int32_t* __restrict__ row_graph,
                                                                const int64_t* __restrict__ vtx_off, const unsigned* __restrict__ keep,
-                                                               const int64_t* __restrict__ kpre, int64_t* __restrict__ rpp,
+                                                               const int64_t* __restrict__ kpre, const int64_t* __restrict__ rpp,
+                                                               const int32_t* __restrict__ dplus, const int64_t* __restrict__ rp4,
                                                                int32_t* __restrict__ colp, int32_t* __restrict__ colr,
                                                                int2* __restrict__ rspan) {
     __shared__ MpTile<BATCH> S;
     __shared__ int s_mn[kMpTile + 1], s_mx[kMpTile + 1];
     const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0) rpp[0] = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         for (int k = threadIdx.x; k <= kMpTile; k += blockDim.x) {
             s_mn[k] = 0x7fffffff;
@@ -378,6 +395,10 @@ __global__ void __launch_bounds__(kMpThreads) k_orient_scatter(int64_t n, int64_
         mp_tile<BATCH>(S, t, n, coord, rp, row_graph, vtx_off);
         const int64_t i0 = S.i0, j0 = S.j0;
         const int ne = S.ne, nr = S.nr;
+        // colr position of a kept entry = its colp position + the padding of
+        // the rows before its row (du is not needed here and is reused)
+        for (int k = threadIdx.x; k < nr; k += blockDim.x) S.du[k] = (int)(rp4[i0 + k] - rpp[i0 + k]);
+        __syncthreads();
         // all loads of the tile first: keep words and lists, then the rank gathers
         unsigned kw[kMpIpt];
         int32_t vv[kMpIpt];
@@ -406,7 +427,7 @@ __global__ void __launch_bounds__(kMpThreads) k_orient_scatter(int64_t n, int64_
                     const int64_t g = j0 + e;
                     const int64_t pos = bits_before(keep, kpre, g);
                     colp[pos] = vv[q];
-                    colr[pos] = rr[q];
+                    colr[pos + S.du[k]] = rr[q];
                     mn = mx = rr[q];
                 }
             }
@@ -430,7 +451,11 @@ __global__ void __launch_bounds__(kMpThreads) k_orient_scatter(int64_t n, int64_
         __syncthreads();
         for (int k = threadIdx.x; k < nr; k += blockDim.x) {
             const int64_t u = i0 + k;
-            if (k < S.nend) rpp[u + 1] = bits_before(keep, kpre, j0 + S.cs[k + 1]);
+            if (k < S.nend) {  // the row ends here: pad its colr row
+                const int d = dplus[u];
+                const int64_t b = rp4[u];
+                for (int j = d; j < ((d + 3) & ~3); ++j) colr[b + j] = -1;
+            }
             if (k < S.nend && (k > 0 || S.first_full)) {
                 rspan[u] = make_int2(s_mn[k], s_mx[k]);
             } else if (s_mx[k] >= 0) {
@@ -442,10 +467,6 @@ __global__ void __launch_bounds__(kMpThreads) k_orient_scatter(int64_t n, int64_
     }
 }
 
-__global__ void k_dplus(int64_t n, const int64_t* __restrict__ rpp, int32_t* __restrict__ dplus) {
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
-        dplus[u] = (int32_t)(rpp[u + 1] - rpp[u]);
-}
 
 // ============================================================================
 // a-4  partition (Alg. 2 Partition; Sec. 4.2.2 dynamic grouping).
@@ -664,7 +685,9 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     A((void**)&o->dplus, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->rank, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->perm, sizeof(int32_t) * std::max<int64_t>(n, 1));
-    A((void**)&o->colr, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 4));
+    // padded rank-id rows: at most 3 pad slots per non-empty row
+    A((void**)&o->colr, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 3 * std::min(n, m) + 4));
+    A((void**)&o->rp4, sizeof(int64_t) * n1);
     A((void**)&o->rspan, sizeof(int2) * std::max<int64_t>(n, 1));
     A((void**)&o->prp, sizeof(int64_t) * n1);
     A((void**)&o->pcol, sizeof(int32_t) * std::max<int64_t>(m, 1));
@@ -680,7 +703,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         return set_err(ctx, TC_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
     deg = o->deg;
-    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 6 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
+    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 3 + sizeof(int32_t) * (3 * m + 3 * std::min(n, m) + 6 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
                          + (batch ? sizeof(int32_t) * n : 0));
     cudaMemsetAsync(o->dc, 0, sizeof(DevCounters), s);
 
@@ -786,18 +809,16 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         PhaseScope ph(ctx, kPhOrientScan, s);
         k_popc<<<grid_for(kw, 256, ns), 256, 0, s>>>(keep, kw, wpc);
         scan_i32_to_i64(wpc, kpre, kw, wtmp, wtb, s);
-        ctx->launches += 4;
+        // row offsets, d+, and the padded colr offsets (pc serves as scratch)
+        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rpp, o->dplus, pc);
+        scan_i32_to_i64(pc, o->rp4, n, wtmp, wtb, s);
+        ctx->launches += 8;
     }
     {
         PhaseScope ph(ctx, kPhOrientScatter, s);
-        cudaMemsetAsync(o->rpp, 0, sizeof(int64_t), s);
         if (nt1 > 0) {
-            if (batch) k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
-            else k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
-            TC_LAUNCH(ctx);
-        }
-        if (n > 0) {
-            k_dplus<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->rpp, o->dplus);
+            if (batch) k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre, o->rpp, o->dplus, o->rp4, o->colp, o->colr, o->rspan);
+            else k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre, o->rpp, o->dplus, o->rp4, o->colp, o->colr, o->rspan);
             TC_LAUNCH(ctx);
         }
     }

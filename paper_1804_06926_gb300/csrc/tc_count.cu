@@ -41,11 +41,12 @@ struct CountArgs {
     unsigned long long* totals;   // [G] (batch) or [1]
     unsigned long long* t;        // per-vertex counts or nullptr
     const int32_t* row_graph;     // batch: graph of each vertex, else nullptr
-    const int32_t* colr;          // oriented lists in rank ids
+    const int32_t* colr;          // oriented lists in rank ids, rows at rp4[u], padded with -1 to 4k entries
+    const int64_t* rp4;           // row offsets of colr (multiples of 4)
     const int32_t* perm;          // rank id -> vertex id
     const int2* rspan;            // smallest and largest rank id of each oriented row
     int bitmap_bits;              // max span (rank ids) of a bitmap table; 0 = off
-    int direct_span;              // max span of a direct 16-bit cell table; 0 = off
+    int direct_span;              // max span of a direct cell table (32-bit cells up to half of it); 0 = off
     int u_ints;                   // ints of the table region of k_count_cta
     int64_t n;
     int shard, nshards;           // this launch covers shard `shard` of `nshards` equal parts of the work
@@ -135,7 +136,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 #define TC_CTA_VEC 4
 #endif
 #ifndef TC_CTA_LANE_SHIFT
-#define TC_CTA_LANE_SHIFT 3
+#define TC_CTA_LANE_SHIFT 5
 #endif
 constexpr int kVec = TC_CTA_VEC;  // 16-byte vector loads in flight per lane
 
@@ -191,7 +192,16 @@ struct CtaScratch {
 constexpr int kModeHash = 0;
 constexpr int kModeBitmap = 1;
 constexpr int kModeBsearch = 2;
-constexpr int kModeDirect = 3;   // one 16-bit cell per rank id of the span: 0 = absent, 1 + hits
+constexpr int kModeDirect = 3;   // one 16-bit cell per rank id of the span
+constexpr int kModeDirect32 = 4; // one 32-bit cell per rank id, for spans up to direct_span / 2
+// Direct cells: a key's cell holds a marker (top bit) plus its hits.  With
+// per-vertex counts every probe inside the span is one shared atomic add whose
+// returned old value carries the marker, so a probe needs no separate load;
+// cells of rank ids that are not keys collect junk counts (at most one per
+// partner of the item, below the marker) and the whole span is cleared after
+// the item.
+constexpr unsigned kMark32 = 0x80000000u;
+constexpr unsigned kMark16 = 0x8000u;
 
 struct Table {
     const int* keys;
@@ -200,6 +210,7 @@ struct Table {
     const unsigned* bits;
     const unsigned short* pre;
     unsigned short* cell;  // direct mode
+    unsigned* cell32;      // direct mode, 32-bit cells
     int lo, span;
 };
 
@@ -231,8 +242,10 @@ __device__ __forceinline__ bool table_hit(const Table& t, int x) {
 }
 
 // Lanes per partner for a list-length class c (lists of 2^c .. 2^(c+1)-1
-// elements): one lane up to 15 elements, then doubling up to a full warp, so
-// that every lane of a task loads 2 to 4 aligned 16-byte vectors per list.
+// elements): one lane up to 2^(TC_CTA_LANE_SHIFT+1)-1 elements, then doubling
+// up to a full warp, so that every lane of a task loads 2^(TC_CTA_LANE_SHIFT-2)
+// to 2^(TC_CTA_LANE_SHIFT-1) aligned 16-byte vectors of its list (8 to 16 with
+// the default shift of 5).
 __device__ __forceinline__ int class_lanes(int c) { return 1 << min(max(c - TC_CTA_LANE_SHIFT, 0), 5); }
 
 // One warp intersects the partners pb+first, pb+first+stride, ... (in groups
@@ -342,6 +355,91 @@ __device__ __forceinline__ int probe_list(const Table& tb, const int32_t* __rest
     return myc;
 }
 
+// Shared-memory add under a predicate, with no branch around it: the per-hit
+// counter update of a probe costs the same instructions whether it hits or not.
+__device__ __forceinline__ void red_shared_if(bool p, const void* addr, unsigned v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.u32 [%0], %1;\n\t}" ::"r"(a), "r"(v),
+        "r"((unsigned)p)
+        : "memory");
+}
+
+// Shared-memory atomic add under a predicate, returning the old value (0 when
+// the predicate is false).
+__device__ __forceinline__ unsigned atom_shared_add_if(bool p, const void* addr, unsigned v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\tmov.u32 %0, 0;\n\t@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
+        : "=r"(r)
+        : "r"(a), "r"(v), "r"((unsigned)p)
+        : "memory");
+    return r;
+}
+
+// Probe one element x of a padded rank-id list (x = -1 is padding and never
+// hits); returns 1 on a hit and counts it for x's per-vertex total when PV.
+template <int MODE, bool PV>
+__device__ __forceinline__ int probe1(const Table& t, int x) {
+    if (MODE == kModeDirect32) {
+        const unsigned off = (unsigned)(x - t.lo);
+        const bool in = off < (unsigned)t.span;
+        if (PV) return (int)(atom_shared_add_if(in, t.cell32 + off, 1u) >> 31);
+        const unsigned c = in ? t.cell32[off] : 0u;
+        return c != 0u ? 1 : 0;
+    } else if (MODE == kModeDirect) {
+        const unsigned off = (unsigned)(x - t.lo);
+        const bool in = off < (unsigned)t.span;
+        if (PV) {
+            const unsigned sh = (off & 1u) << 4;
+            return (int)((atom_shared_add_if(in, t.cell + (off & ~1u), 1u << sh) >> (15u + sh)) & 1u);
+        }
+        const unsigned c = in ? (unsigned)t.cell[off] : 0u;
+        return c != 0u ? 1 : 0;
+    } else if (MODE == kModeBitmap) {
+        const unsigned off = (unsigned)(x - t.lo);
+        const bool in = off < (unsigned)t.span;
+        const unsigned word = in ? t.bits[off >> 5] : 0u;
+        const unsigned b = off & 31u;
+        const bool hit = (word >> b) & 1u;
+        if (PV) {
+            const int ord = hit ? (int)t.pre[off >> 5] + __popc(word & ((1u << b) - 1u)) : 0;
+            red_shared_if(hit, t.cnts + ord, 1u);
+        }
+        return hit ? 1 : 0;
+    } else {
+        if (x < 0) return 0;
+        const int h = table_find_z(t.keys, t.logS, x);
+        if (h < 0) return 0;
+        if (PV) atomicAdd(&t.cnts[h], 1);
+        return 1;
+    }
+}
+
+// probe_list for the padded rank-id rows: the list starts 16-byte aligned and
+// its last vector is filled up with -1, so every vector is probed whole.
+template <int MODE, bool PV>
+__device__ __forceinline__ int probe_list_padded(const Table& tb, const int32_t* __restrict__ L, int64_t qb, int dq,
+                                                 int r, int G) {
+    const int4* __restrict__ lv = reinterpret_cast<const int4*>(L + qb);
+    const int nv = (dq + 3) >> 2;
+    int myc = 0;
+    for (int v0 = r; v0 < nv; v0 += G * kVec) {
+        int4 w[kVec];
+#pragma unroll
+        for (int u = 0; u < kVec; ++u) {
+            const int vv = v0 + u * G;
+            w[u] = vv < nv ? lv[vv] : make_int4(-1, -1, -1, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < kVec; ++u)
+            myc += probe1<MODE, PV>(tb, w[u].x) + probe1<MODE, PV>(tb, w[u].y) + probe1<MODE, PV>(tb, w[u].z) +
+                   probe1<MODE, PV>(tb, w[u].w);
+    }
+    return myc;
+}
+
 // Intersect the item's partners [pb, pe) with the table.  Partners are taken
 // pmax at a time, counting-sorted by length class, and cut into warp tasks of
 // 32/G partners of one class with G lanes per partner (the dynamic grouping by
@@ -351,7 +449,8 @@ __device__ __forceinline__ int probe_list(const Table& tb, const int32_t* __rest
 // stay in registers until a G-lane reduction.
 template <bool PV, int MODE>
 __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, const int32_t* __restrict__ L,
-                                                           const Table& tb, int64_t pbase, int pb, int pe, int pmax,
+                                                           const int64_t* __restrict__ LR, const Table& tb,
+                                                           int64_t pbase, int pb, int pe, int pmax,
                                                            const CtaScratch& sc) {
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -372,8 +471,8 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             rb[k] = 0;
             if (i < NP) {
                 rq[k] = a.pcol[pbase + c0 + i];
-                rb[k] = a.rpp[rq[k]];
-                rd[k] = (int)(a.rpp[rq[k] + 1] - rb[k]);
+                rb[k] = LR[rq[k]];
+                rd[k] = a.dp[rq[k]];
                 rc[k] = min(kClasses - 1, 31 - __clz(rd[k]));
                 rs[k] = atomicAdd(&sc.ccnt[rc[k]], 1);
             }
@@ -420,7 +519,8 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             const bool valid = i < sc.coff[c] + sc.ccnt[c];
             const int dq = valid ? sc.dq[i] : 0;
             const int64_t qb = valid ? sc.qb[i] : 0;
-            int myc = probe_list<MODE, PV>(tb, L, qb, dq, r, G);
+            int myc = MODE == kModeBsearch ? probe_list<MODE, PV>(tb, L, qb, dq, r, G)
+                                           : probe_list_padded<MODE, PV>(tb, L, qb, dq, r, G);
             for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
             if (r == 0 && valid && myc) {
                 acc += (unsigned long long)myc;
@@ -437,7 +537,7 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
 static int cta_table_ints(int cap, int bitmap_bits) {
     const int words = bitmap_bits / 32;
     const int bm = words + (words + 1) / 2 + cap;
-    return std::max(8 * cap, bm);
+    return (std::max(8 * cap, bm) + 3) & ~3;  // whole 16-byte vectors (span clears)
 }
 
 // partners sorted per sub-chunk: 2 per thread
@@ -463,7 +563,10 @@ __device__ __forceinline__ void block_minmax(int& mn, int& mx, int* red) {
 
 // BIG = false: at most 256 threads, registers capped for 5 resident CTAs per SM
 template <bool PV, int PROBE, bool BIG>
-__global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(CountArgs a) {
+#ifndef TC_CTA_MIN_BLOCKS
+#define TC_CTA_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS) k_count_cta(CountArgs a) {
     extern __shared__ __align__(16) int smem[];
     int* U = smem;
     CtaScratch sc;
@@ -488,6 +591,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
     // hash mode probes rank ids (so that a short span can use the bitmap);
     // the binary-search mode probes the id-sorted lists
     const int32_t* __restrict__ L = PROBE == kProbeHash ? a.colr : a.colp;
+    const int64_t* __restrict__ LR = PROBE == kProbeHash ? a.rp4 : a.rpp;
     const unsigned long long n_all = min(*a.n_items, a.items_cap);
     const unsigned long long it_lo = n_all * a.shard / a.nshards;
     const unsigned long long n_items = n_all * (a.shard + 1) / a.nshards;
@@ -498,8 +602,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
         s_valid = it < n_items;
         if (s_valid) {
             s_cur = a.items[it];
-            s_r0 = a.rpp[s_cur.p];
-            s_r1 = a.rpp[s_cur.p + 1];
+            s_r0 = LR[s_cur.p];
+            s_r1 = s_r0 + a.dp[s_cur.p];
         }
     }
     for (;;) {
@@ -537,7 +641,11 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
                 }
                 block_minmax(mn, mx, s_red);
             }
-            if (mx - mn < a.direct_span && (mx - mn + 2) / 2 <= a.u_ints) {
+            if (mx - mn < a.direct_span / 2 && mx - mn + 1 <= a.u_ints) {
+                mode = kModeDirect32;
+                tb.lo = mn;
+                tb.span = mx - mn + 1;
+            } else if (mx - mn < a.direct_span && (mx - mn + 2) / 2 <= a.u_ints && item.pe - item.pb < 0x8000) {
                 mode = kModeDirect;
                 tb.lo = mn;
                 tb.span = mx - mn + 1;
@@ -549,9 +657,12 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
         }
         // the table region is all zeros here: every item resets what it set
         int nflush = 0;
-        if (mode == kModeDirect) {
+        if (mode == kModeDirect32) {
+            tb.cell32 = reinterpret_cast<unsigned*>(U);
+            for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell32[L[lb + i] - tb.lo] = kMark32;
+        } else if (mode == kModeDirect) {
             tb.cell = reinterpret_cast<unsigned short*>(U);
-            for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell[L[lb + i] - tb.lo] = 1;
+            for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell[L[lb + i] - tb.lo] = (unsigned short)kMark16;
         } else if (mode == kModeBitmap) {
             const int W = (tb.span + 31) >> 5;
             unsigned* bits = reinterpret_cast<unsigned*>(U);
@@ -593,20 +704,32 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
         }
         __syncthreads();
         unsigned long long acc;
-        if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        if (mode == kModeDirect32) acc = cta_partners<PV, kModeDirect32>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else acc = cta_partners<PV, kModeBsearch>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
         // per-vertex counts of the table's keys, and reset of what this item set
-        if (mode == kModeDirect) {
-            for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                const int x = L[lb + i];
-                const int c = (int)tb.cell[x - tb.lo] - 1;
-                if (PV && c > 0) atomicAdd(&a.t[a.perm[x]], (unsigned long long)c);
-                tb.cell[x - tb.lo] = 0;
+        if (mode == kModeDirect32 || mode == kModeDirect) {
+            if (PV) {
+                for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                    const int x = L[lb + i];
+                    const unsigned c = mode == kModeDirect32 ? tb.cell32[x - tb.lo] & ~kMark32
+                                                             : (unsigned)tb.cell[x - tb.lo] & ~kMark16;
+                    if (c) atomicAdd(&a.t[a.perm[x]], (unsigned long long)c);
+                }
+                __syncthreads();
+                // clear the whole span (junk counts of non-keys included)
+                const int nz = mode == kModeDirect32 ? (tb.span + 3) >> 2 : (tb.span + 7) >> 3;
+                uint4* z = reinterpret_cast<uint4*>(U);
+                for (int i = threadIdx.x; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+            } else if (mode == kModeDirect32) {
+                for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell32[L[lb + i] - tb.lo] = 0u;
+            } else {
+                for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell[L[lb + i] - tb.lo] = 0;
             }
         } else if (mode == kModeBitmap) {
             if (PV) {
@@ -647,8 +770,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 5) k_count_cta(Cou
             s_valid = nit < n_items;
             if (s_valid) {
                 s_cur = nitem;
-                s_r0 = a.rpp[nitem.p];
-                s_r1 = a.rpp[nitem.p + 1];
+                s_r0 = LR[nitem.p];
+                s_r1 = s_r0 + a.dp[nitem.p];
             }
         }
     }
@@ -850,6 +973,7 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.shard = shard;
     a.nshards = nshards;
     a.colr = o->colr;
+    a.rp4 = o->rp4;
     a.perm = o->perm;
     a.rspan = o->rspan;
     a.bitmap_bits = tun.bitmap_bits;

@@ -53,7 +53,8 @@ struct tc_ocsr {
     int32_t* deg = nullptr;     // [n] undirected degrees
     int32_t* rank = nullptr;    // [n] position of each vertex in (degree, id) order
     int32_t* perm = nullptr;    // [n] inverse of rank
-    int32_t* colr = nullptr;    // [m] colp relabelled to rank ids (same row layout)
+    int32_t* colr = nullptr;    // colp relabelled to rank ids, each row at rp4[u] padded with -1 to a multiple of 4
+    int64_t* rp4 = nullptr;     // [n+1] row offsets of colr (multiples of 4: rows are 16-byte aligned)
     int2* rspan = nullptr;      // [n] smallest and largest rank id in each oriented row
     int64_t* prp = nullptr;     // [n+1] partner row offsets
     int32_t* pcol = nullptr;    // [m] partners (only the first n_pivot_edges used)
