@@ -196,6 +196,14 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ r
 constexpr int kMpThreads = 256;
 constexpr int kMpIpt = 8;
 constexpr int kMpTile = kMpThreads * kMpIpt;
+// resident CTAs per SM the tile kernels are compiled for (registers permitting):
+// they wait on scattered loads, so more warps in flight hide more latency
+#ifndef TC_MP_MIN_BLOCKS
+#define TC_MP_MIN_BLOCKS 6
+#endif
+#ifndef TC_MP_SCATTER_MIN_BLOCKS
+#define TC_MP_SCATTER_MIN_BLOCKS 5
+#endif
 
 int64_t mp_tiles(int64_t n, int64_t nnz) { return (n + nnz + kMpTile - 1) / kMpTile; }
 
@@ -319,7 +327,7 @@ __global__ void k_popc(const unsigned* __restrict__ mask, int64_t nw, int32_t* _
 // vectors; it also records each row's smallest and largest rank id.
 // ============================================================================
 template <bool BATCH>
-__global__ void __launch_bounds__(kMpThreads) k_orient_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
+__global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                              const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                              const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
                                                              const int64_t* __restrict__ vtx_off, unsigned* __restrict__ keep,
@@ -376,7 +384,7 @@ __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned
 }
 
 template <bool BATCH>
-__global__ void __launch_bounds__(kMpThreads) k_orient_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
+__global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                                const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                                const int32_t* __restrict__ rank, const int32_t* __restrict__ row_graph,
                                                                const int64_t* __restrict__ vtx_off, const unsigned* __restrict__ keep,
@@ -555,7 +563,7 @@ __global__ void k_pivot_offsets(int64_t n, const int64_t* __restrict__ rpp, cons
 }
 
 // nv[p] counts down from nV(p) while p's V-part is filled.
-__global__ void __launch_bounds__(kMpThreads) k_pivot_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
+__global__ void __launch_bounds__(kMpThreads, 1) k_pivot_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                               const int64_t* __restrict__ rpp, const int32_t* __restrict__ colp,
                                                               const unsigned* __restrict__ umask, const unsigned* __restrict__ vmask,
                                                               const int64_t* __restrict__ upre, const int64_t* __restrict__ vpre,
