@@ -322,9 +322,10 @@ __global__ void k_popc(const unsigned* __restrict__ mask, int64_t nw, int32_t* _
 // position of a kept entry in the oriented CSR is the number of kept entries
 // before it (a prefix count over the bitmask) and rpp[u] is that count at
 // row_ptr[u] (k_rows).  Pass 2 scatters the kept neighbours: vertex ids to
-// colp, rank ids to colr, whose rows start at multiples of 4 (rp4) and are
-// padded with -1 so that the count kernels read them as whole aligned 16-byte
-// vectors; it also records each row's smallest and largest rank id.
+// colp, rank ids to colr, whose rows start at multiples of 4 (colr_row) and
+// are padded with -1 (colr is cleared to -1 first) so that the count kernels
+// read them as whole aligned 16-byte vectors; it also records each row's
+// smallest and largest rank id.
 // ============================================================================
 template <bool BATCH>
 __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
@@ -368,18 +369,13 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(i
     }
 }
 
-// rpp[u] = kept entries before row u; d+(u); the padded length of u's colr row
+// rpp[u] = kept entries before row u, and d+(u)
 __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned* __restrict__ keep,
-                       const int64_t* __restrict__ kpre, int64_t* __restrict__ rpp, int32_t* __restrict__ dplus,
-                       int32_t* __restrict__ pad4) {
+                       const int64_t* __restrict__ kpre, int64_t* __restrict__ rpp, int32_t* __restrict__ dplus) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = bits_before(keep, kpre, rp[u]);
         rpp[u] = s;
-        if (u < n) {
-            const int d = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
-            dplus[u] = d;
-            pad4[u] = (d + 3) & ~3;
-        }
+        if (u < n) dplus[u] = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
     }
 }
 
@@ -389,7 +385,6 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                                                                const int32_t* __restrict__ rank, const int32_t* __restrict__ row_graph,
                                                                const int64_t* __restrict__ vtx_off, const unsigned* __restrict__ keep,
                                                                const int64_t* __restrict__ kpre, const int64_t* __restrict__ rpp,
-                                                               const int32_t* __restrict__ dplus, const int64_t* __restrict__ rp4,
                                                                int32_t* __restrict__ colp, int32_t* __restrict__ colr,
                                                                int2* __restrict__ rspan) {
     __shared__ MpTile<BATCH> S;
@@ -405,7 +400,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
         const int ne = S.ne, nr = S.nr;
         // colr position of a kept entry = its colp position + the padding of
         // the rows before its row (du is not needed here and is reused)
-        for (int k = threadIdx.x; k < nr; k += blockDim.x) S.du[k] = (int)(rp4[i0 + k] - rpp[i0 + k]);
+        for (int k = threadIdx.x; k < nr; k += blockDim.x) S.du[k] = (int)(colr_row(rpp, i0 + k) - rpp[i0 + k]);
         __syncthreads();
         // all loads of the tile first: keep words and lists, then the rank gathers
         unsigned kw[kMpIpt];
@@ -459,11 +454,6 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
         __syncthreads();
         for (int k = threadIdx.x; k < nr; k += blockDim.x) {
             const int64_t u = i0 + k;
-            if (k < S.nend) {  // the row ends here: pad its colr row
-                const int d = dplus[u];
-                const int64_t b = rp4[u];
-                for (int j = d; j < ((d + 3) & ~3); ++j) colr[b + j] = -1;
-            }
             if (k < S.nend && (k > 0 || S.first_full)) {
                 rspan[u] = make_int2(s_mn[k], s_mx[k]);
             } else if (s_mx[k] >= 0) {
@@ -693,9 +683,8 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     A((void**)&o->dplus, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->rank, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->perm, sizeof(int32_t) * std::max<int64_t>(n, 1));
-    // padded rank-id rows: at most 3 pad slots per non-empty row
-    A((void**)&o->colr, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 3 * std::min(n, m) + 4));
-    A((void**)&o->rp4, sizeof(int64_t) * n1);
+    // padded rank-id rows (colr_row): at most m + 3n + 3 entries
+    A((void**)&o->colr, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 3 * n + 4));
     A((void**)&o->rspan, sizeof(int2) * std::max<int64_t>(n, 1));
     A((void**)&o->prp, sizeof(int64_t) * n1);
     A((void**)&o->pcol, sizeof(int32_t) * std::max<int64_t>(m, 1));
@@ -711,7 +700,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         return set_err(ctx, TC_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
     deg = o->deg;
-    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 3 + sizeof(int32_t) * (3 * m + 3 * std::min(n, m) + 6 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
+    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 9 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
                          + (batch ? sizeof(int32_t) * n : 0));
     cudaMemsetAsync(o->dc, 0, sizeof(DevCounters), s);
 
@@ -817,16 +806,17 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         PhaseScope ph(ctx, kPhOrientScan, s);
         k_popc<<<grid_for(kw, 256, ns), 256, 0, s>>>(keep, kw, wpc);
         scan_i32_to_i64(wpc, kpre, kw, wtmp, wtb, s);
-        // row offsets, d+, and the padded colr offsets (pc serves as scratch)
-        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rpp, o->dplus, pc);
-        scan_i32_to_i64(pc, o->rp4, n, wtmp, wtb, s);
-        ctx->launches += 8;
+        // row offsets and d+
+        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rpp, o->dplus);
+        ctx->launches += 5;
     }
     {
         PhaseScope ph(ctx, kPhOrientScatter, s);
+        // padding (and the gaps between rows) of colr read as -1
+        cudaMemsetAsync(o->colr, 0xff, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 3 * n + 4), s);
         if (nt1 > 0) {
-            if (batch) k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre, o->rpp, o->dplus, o->rp4, o->colp, o->colr, o->rspan);
-            else k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre, o->rpp, o->dplus, o->rp4, o->colp, o->colr, o->rspan);
+            if (batch) k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
+            else k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
             TC_LAUNCH(ctx);
         }
     }

@@ -41,8 +41,7 @@ struct CountArgs {
     unsigned long long* totals;   // [G] (batch) or [1]
     unsigned long long* t;        // per-vertex counts or nullptr
     const int32_t* row_graph;     // batch: graph of each vertex, else nullptr
-    const int32_t* colr;          // oriented lists in rank ids, rows at rp4[u], padded with -1 to 4k entries
-    const int64_t* rp4;           // row offsets of colr (multiples of 4)
+    const int32_t* colr;          // oriented lists in rank ids, row u at colr_row(rpp, u), padded with -1
     const int32_t* perm;          // rank id -> vertex id
     const int2* rspan;            // smallest and largest rank id of each oriented row
     int bitmap_bits;              // max span (rank ids) of a bitmap table; 0 = off
@@ -325,6 +324,75 @@ __device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, 
     return acc;
 }
 
+// warp_partners over the padded rank-id lists, flattened by whole 16-byte
+// vectors: window k0 .. k0+31 puts vector k0+lane of the 32 partners'
+// concatenated vector sequence on lane `lane` (owner found as in
+// warp_partners), and each lane probes the 4 elements of its vector in the
+// zero-encoded hash table of the pivot (padding -1 never hits).  Per-partner
+// hit counts come from one ballot per vector component.
+constexpr int kWarpVec = 2;
+
+template <bool PV>
+__device__ __forceinline__ unsigned long long warp_partners_vec(const CountArgs& a, const int* keys, int* cnts,
+                                                                int logS, int64_t pbase, int pb, int pe) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned le_mask = lane == 31 ? FULL : ((2u << lane) - 1u);
+    const int4* __restrict__ lv = reinterpret_cast<const int4*>(a.colr);
+    unsigned long long acc = 0;
+    for (int g0 = pb; g0 < pe; g0 += 32) {
+        const int i = g0 + lane;
+        const bool valid = i < pe;
+        const int q = valid ? a.pcol[pbase + i] : 0;
+        const int64_t qv = valid ? (colr_row(a.rpp, q) >> 2) : 0;   // first vector of q's row
+        const int nvq = valid ? (a.dp[q] + 3) >> 2 : 0;   // >= 1: partner lists are non-empty
+        const int incl = warp_incl_scan_i(nvq);
+        const int tot = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - nvq;
+        const int64_t base = qv - excl;  // vector k of the flattened sequence owned by q is lv[base + k]
+        int myc = 0, P = 0;
+        for (int k0 = 0; k0 < tot; k0 += 32 * kWarpVec) {
+            int4 w[kWarpVec];
+#pragma unroll
+            for (int u = 0; u < kWarpVec; ++u) {
+                const int s = excl - (k0 + 32 * u);
+                const unsigned bit = (valid && s >= 0 && s < 32) ? (1u << s) : 0u;
+                const unsigned M = __reduce_or_sync(FULL, bit);
+                const int j = P + __popc(M & le_mask) - 1;
+                P += __popc(M);
+                const int64_t bj = __shfl_sync(FULL, base, j & 31);
+                const int k = k0 + 32 * u + lane;
+                w[u] = k < tot ? lv[bj + k] : make_int4(-1, -1, -1, -1);
+            }
+#pragma unroll
+            for (int u = 0; u < kWarpVec; ++u) {
+                const int xs[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+                const int s = excl - (k0 + 32 * u);
+                const int lo = max(s, 0), hi = min(s + nvq, 32);
+                const unsigned rm = lo < hi ? ((hi >= 32 ? FULL : ((1u << hi) - 1u)) & (FULL << lo)) : 0u;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    bool hit = false;
+                    if (xs[c] >= 0) {
+                        const int h = table_find_z(keys, logS, xs[c]);
+                        if (h >= 0) {
+                            hit = true;
+                            if (PV) atomicAdd(&cnts[h], 1);
+                        }
+                    }
+                    const unsigned hm = __ballot_sync(FULL, hit);
+                    myc += __popc(hm & rm);
+                }
+            }
+        }
+        if (valid && myc) {
+            acc += (unsigned long long)myc;
+            if (PV) atomicAdd(&a.t[q], (unsigned long long)myc);
+        }
+    }
+    return acc;
+}
+
 // Lane r of the G lanes that share one partner list (start qb, length dq in
 // L) probes the list's elements in the table, reading the list as aligned
 // 16-byte vectors r, r+G, ... (the lists are padded by 4 elements), kVec
@@ -449,8 +517,7 @@ __device__ __forceinline__ int probe_list_padded(const Table& tb, const int32_t*
 // stay in registers until a G-lane reduction.
 template <bool PV, int MODE>
 __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, const int32_t* __restrict__ L,
-                                                           const int64_t* __restrict__ LR, const Table& tb,
-                                                           int64_t pbase, int pb, int pe, int pmax,
+                                                           const Table& tb, int64_t pbase, int pb, int pe, int pmax,
                                                            const CtaScratch& sc) {
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -471,7 +538,7 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             rb[k] = 0;
             if (i < NP) {
                 rq[k] = a.pcol[pbase + c0 + i];
-                rb[k] = LR[rq[k]];
+                rb[k] = MODE == kModeBsearch ? a.rpp[rq[k]] : colr_row(a.rpp, rq[k]);
                 rd[k] = a.dp[rq[k]];
                 rc[k] = min(kClasses - 1, 31 - __clz(rd[k]));
                 rs[k] = atomicAdd(&sc.ccnt[rc[k]], 1);
@@ -591,7 +658,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
     // hash mode probes rank ids (so that a short span can use the bitmap);
     // the binary-search mode probes the id-sorted lists
     const int32_t* __restrict__ L = PROBE == kProbeHash ? a.colr : a.colp;
-    const int64_t* __restrict__ LR = PROBE == kProbeHash ? a.rp4 : a.rpp;
+    constexpr bool kPadded = PROBE == kProbeHash;  // colr rows (colr_row) or colp rows (rpp)
     const unsigned long long n_all = min(*a.n_items, a.items_cap);
     const unsigned long long it_lo = n_all * a.shard / a.nshards;
     const unsigned long long n_items = n_all * (a.shard + 1) / a.nshards;
@@ -602,7 +669,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
         s_valid = it < n_items;
         if (s_valid) {
             s_cur = a.items[it];
-            s_r0 = LR[s_cur.p];
+            s_r0 = kPadded ? colr_row(a.rpp, s_cur.p) : a.rpp[s_cur.p];
             s_r1 = s_r0 + a.dp[s_cur.p];
         }
     }
@@ -704,11 +771,11 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
         }
         __syncthreads();
         unsigned long long acc;
-        if (mode == kModeDirect32) acc = cta_partners<PV, kModeDirect32>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else acc = cta_partners<PV, kModeBsearch>(a, L, LR, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        if (mode == kModeDirect32) acc = cta_partners<PV, kModeDirect32>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
@@ -770,7 +837,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
             s_valid = nit < n_items;
             if (s_valid) {
                 s_cur = nitem;
-                s_r0 = LR[nitem.p];
+                s_r0 = kPadded ? colr_row(a.rpp, nitem.p) : a.rpp[nitem.p];
                 s_r1 = s_r0 + a.dp[nitem.p];
             }
         }
@@ -797,19 +864,40 @@ __global__ void __launch_bounds__(256) k_count_warp(CountArgs a, int wcap) {
         if (it >= n_items) break;
         const Item item = a.items[it];
         const int p = item.p;
-        const int64_t lb = a.rpp[p];
-        const int len = (int)(a.rpp[p + 1] - lb);
-        int logS, S;
         if (PROBE == kProbeHash) {
-            logS = max(5, 32 - __clz(4 * len - 1));  // load factor <= 1/4
-            S = 1 << logS;
+            // rank-id hash of N+(p) (keys x+1, 0 = empty); partners' padded rank-id lists
+            const int64_t lb = colr_row(a.rpp, p);
+            const int len = a.dp[p];
+            const int logS = max(5, 32 - __clz(4 * len - 1));  // load factor <= 1/4
+            const int S = 1 << logS;
             for (int i = lane; i < S; i += 32) {
-                keys[i] = -1;
+                keys[i] = 0;
                 if (PV) cnts[i] = 0;
             }
             __syncwarp();
-            for (int i = lane; i < len; i += 32) table_insert(keys, logS, a.colp[lb + i]);
-        } else {
+            for (int i = lane; i < len; i += 32) table_insert_z(keys, logS, a.colr[lb + i]);
+            __syncwarp();
+            unsigned long long acc = warp_partners_vec<PV>(a, keys, cnts, logS, a.prp[p], item.pb, item.pe);
+            __syncwarp();
+            if (PV) {
+                for (int i = lane; i < S; i += 32) {
+                    const int c = cnts[i];
+                    if (c) atomicAdd(&a.t[a.perm[keys[i] - 1]], (unsigned long long)c);
+                }
+            }
+            acc = warp_sum_u64(acc);
+            if (lane == 0 && acc) {
+                const int g = a.row_graph ? a.row_graph[p] : 0;
+                atomicAdd(&a.totals[g], acc);
+                if (PV) atomicAdd(&a.t[p], acc);
+            }
+            __syncwarp();
+            continue;
+        }
+        const int64_t lb = a.rpp[p];
+        const int len = (int)(a.rpp[p + 1] - lb);
+        int logS, S;
+        {
             logS = 0;
             S = len;
             for (int i = lane; i < len; i += 32) {
@@ -973,7 +1061,6 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.shard = shard;
     a.nshards = nshards;
     a.colr = o->colr;
-    a.rp4 = o->rp4;
     a.perm = o->perm;
     a.rspan = o->rspan;
     a.bitmap_bits = tun.bitmap_bits;

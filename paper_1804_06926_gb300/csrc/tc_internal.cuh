@@ -43,6 +43,16 @@ struct Tuning {
 
 }  // namespace tc
 
+namespace tc {
+// Start of row u in colr: rpp[u] + 3u rounded up to a multiple of 4.  Rows
+// are 16-byte aligned and disjoint: the gap to the next start is a multiple
+// of 4 of at least d+(u), so each row has room for its padding, and no offset
+// array or scan is needed (colr holds at most m + 3n + 3 entries).
+__host__ __device__ __forceinline__ int64_t colr_row(const int64_t* rpp, int64_t u) {
+    return (rpp[u] + 3 * u + 3) & ~(int64_t)3;
+}
+}  // namespace tc
+
 // Library-owned oriented CSR and its work partition.
 struct tc_ocsr {
     int device = 0;
@@ -53,8 +63,7 @@ struct tc_ocsr {
     int32_t* deg = nullptr;     // [n] undirected degrees
     int32_t* rank = nullptr;    // [n] position of each vertex in (degree, id) order
     int32_t* perm = nullptr;    // [n] inverse of rank
-    int32_t* colr = nullptr;    // colp relabelled to rank ids, each row at rp4[u] padded with -1 to a multiple of 4
-    int64_t* rp4 = nullptr;     // [n+1] row offsets of colr (multiples of 4: rows are 16-byte aligned)
+    int32_t* colr = nullptr;    // colp relabelled to rank ids; row u at colr_row(rpp, u), padded with -1 to 4k entries
     int2* rspan = nullptr;      // [n] smallest and largest rank id in each oriented row
     int64_t* prp = nullptr;     // [n+1] partner row offsets
     int32_t* pcol = nullptr;    // [m] partners (only the first n_pivot_edges used)
