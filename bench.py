@@ -520,41 +520,42 @@ def run_serve(args, torch, binding, dev, rank, world):
     lat = np.array(lat)
     # saturated throughput with all slots against one slot, no resident graphs:
     # the gain of overlapping requests on the device
-    def saturated(slots, k):
-        sv = binding.Server(device=dev.index, slots=slots, hbm_budget_bytes=40 << 30)
+    def run_all(sv, ids):
         t0 = time.perf_counter()
-        tks = [(sv.submit(pool[picks[i]].n, pool[picks[i]].row_ptr, pool[picks[i]].col), pool[picks[i]].m)
-               for i in range(k)]
+        tks = [(sv.submit(pool[i].n, pool[i].row_ptr, pool[i].col), pool[i].m) for i in ids]
         e = 0
         for tk, m in tks:
             r = sv.wait(tk, 600000)
             assert r["status"] == 0
             e += m
-        wall_s = time.perf_counter() - t0
+            sv.release(tk)
+        return e, time.perf_counter() - t0
+
+    def saturated_ids(ids, slots, fuse):
+        # one untimed pass fills the server's pinned staging pool, the second is timed
+        sv = binding.Server(device=dev.index, slots=slots, hbm_budget_bytes=40 << 30, batch_graphs=fuse)
+        run_all(sv, ids)
+        b0 = sv.stats()["batches"]
+        e, wall_s = run_all(sv, ids)
+        nb = sv.stats()["batches"] - b0
         sv.close()
-        return e / wall_s, k / wall_s
+        return e / wall_s, len(ids) / wall_s, nb
+
+    def saturated(slots, k, fuse=0):
+        return saturated_ids([int(picks[i]) for i in range(k)], slots, fuse)[:2]
     nsat = min(nreq, args.serve_seq_requests)
     sat_many = saturated(args.slots, nsat)
-    sat_one = saturated(1, nsat)
+    sat_one = saturated(1, nsat, fuse=1)  # one request at a time: one slot, no fused batches
     # the same comparison on the small requests alone (BA graphs and R-MAT s10-s14), where
     # one request does not fill the GPU and overlapping requests is what serving adds
     small_ids = [i for i, g in enumerate(pool) if g.m <= 400000]
     picks_small = rng.choice(small_ids, nsat) if small_ids else picks[:nsat]
 
-    def saturated_small(slots):
-        sv = binding.Server(device=dev.index, slots=slots, hbm_budget_bytes=40 << 30)
-        t0 = time.perf_counter()
-        tks = [(sv.submit(pool[i].n, pool[i].row_ptr, pool[i].col), pool[i].m) for i in picks_small]
-        e = 0
-        for tk, m in tks:
-            r = sv.wait(tk, 600000)
-            assert r["status"] == 0
-            e += m
-        wall_s = time.perf_counter() - t0
-        sv.close()
-        return e / wall_s, len(tks) / wall_s
+    def saturated_small(slots, fuse=0):
+        return saturated_ids([int(i) for i in picks_small], slots, fuse)
     small_many = saturated_small(args.slots)
-    small_one = saturated_small(1)
+    small_slots = saturated_small(args.slots, fuse=1)  # slots overlap, no fused batches
+    small_one = saturated_small(1, fuse=1)
     res = {
         "metric": "served count requests: edges/s, p50/p99 latency", "value": edges / wall, "unit": "edges/s",
         "n_gpus": world, "steps": nreq, "warmup": len(pool), "ms_per_step": wall * 1e3 / nreq,
@@ -570,6 +571,8 @@ def run_serve(args, torch, binding, dev, rank, world):
         "saturated_small": {"requests": nsat, "graphs": "pool members with m <= 400000",
                             "slots": args.slots, "requests_per_s": small_many[1], "edges_per_s": small_many[0],
                             "one_slot_requests_per_s": small_one[1], "one_slot_edges_per_s": small_one[0],
+                            "slots_without_fusing_requests_per_s": small_slots[1],
+                            "fused_batches": small_many[2],
                             "gain": small_many[1] / small_one[1]},
     }
     return res, None

@@ -292,7 +292,12 @@ typedef struct tc_server_config {
     int32_t slots;             /* concurrent requests on the GPU (streams); default 8 */
     int64_t hbm_budget_bytes;  /* default 40 GiB */
     int32_t per_vertex;        /* 1 = also return t(v) */
-    int32_t reserved[7];
+    int32_t batch_graphs;      /* up to this many small requests waiting at the head of the queue
+                                  (host CSR, no TC_VALIDATE, not resident) are fused into one batched
+                                  build + count on one slot; default 32; 1 = never fuse */
+    int64_t batch_nnz;         /* a request is small when its CSR has at most this many entries; a
+                                  fused batch holds at most 8x this many; default 2^20 */
+    int32_t reserved[4];
 } tc_server_config;
 
 typedef struct tc_result {
@@ -317,11 +322,12 @@ tc_status tc_poll(tc_server* s, uint64_t ticket, tc_result* out);
 tc_status tc_wait(tc_server* s, uint64_t ticket, int64_t timeout_ms, tc_result* out);
 /* Forget a finished ticket and free its host result. */
 tc_status tc_release(tc_server* s, uint64_t ticket);
-/* Counters: requests admitted, finished, cache hits, bytes resident. */
+/* Counters: requests admitted, finished, cache hits, bytes resident, fused batches. */
 typedef struct tc_server_stats {
     int64_t submitted, admitted, finished, cache_hits, evictions;
     int64_t resident_bytes, peak_inflight_bytes;
     int32_t peak_inflight;
+    int64_t batches, batched_requests;  /* fused batches run, and the requests they carried */
 } tc_server_stats;
 tc_status tc_server_get_stats(const tc_server* s, tc_server_stats* out);
 

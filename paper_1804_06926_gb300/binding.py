@@ -52,7 +52,8 @@ class tc_batch(C.Structure):
 
 class tc_server_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("hbm_budget_bytes", C.c_int64),
-                ("per_vertex", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("per_vertex", C.c_int32), ("batch_graphs", C.c_int32), ("batch_nnz", C.c_int64),
+                ("reserved", C.c_int32 * 4)]
 
 
 class tc_result(C.Structure):
@@ -73,7 +74,8 @@ class tc_trace(C.Structure):
 class tc_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("finished", C.c_int64),
                 ("cache_hits", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_int64),
-                ("peak_inflight_bytes", C.c_int64), ("peak_inflight", C.c_int32)]
+                ("peak_inflight_bytes", C.c_int64), ("peak_inflight", C.c_int32),
+                ("batches", C.c_int64), ("batched_requests", C.c_int64)]
 
 
 _vp, _P = C.c_void_p, C.POINTER
@@ -384,9 +386,11 @@ class BatchPlan:
 class Server:
     """tc_server: continuous batching of count requests (host CSR inputs)."""
 
-    def __init__(self, device=0, slots=8, hbm_budget_bytes=40 << 30, per_vertex=False, **cfg):
+    def __init__(self, device=0, slots=8, hbm_budget_bytes=40 << 30, per_vertex=False, batch_graphs=0,
+                 batch_nnz=0, **cfg):
         sc = tc_server_config()
         sc.device, sc.slots, sc.hbm_budget_bytes, sc.per_vertex = device, slots, hbm_budget_bytes, int(per_vertex)
+        sc.batch_graphs, sc.batch_nnz = int(batch_graphs), int(batch_nnz)
         self.handle = _vp()
         st = tc_server_create(C.byref(sc), C.byref(make_config(**cfg)), C.byref(self.handle))
         if st != TC_OK:

@@ -7,8 +7,13 @@
 // arrival order whenever a slot is free and the HBM budget holds the resident
 // oriented CSRs plus every in-flight request's estimate; it retires a request
 // when the slot's completion event has fired.  Requests on different slots
-// overlap on the device.  Oriented CSRs built for a non-zero graph_key stay
-// resident (LRU eviction under the budget) so a repeated key skips the build.
+// overlap on the device.  Small requests waiting together at the head of the
+// queue are fused: their CSRs are concatenated (vertex offsets + local ids)
+// and run through the batched build + count of tc_count_batch on one slot, so
+// one launch sequence serves them all; each request still receives its own
+// exact total and per-vertex counts.  Oriented CSRs built for a non-zero
+// graph_key stay resident (LRU eviction under the budget) so a repeated key
+// skips the build.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -50,10 +55,25 @@ struct Request {
     bool done = false;
 };
 
+// A fused batch of small requests on one slot: pinned concatenated inputs and
+// outputs, and the device copies (stream-ordered allocations).
+struct BatchJob {
+    std::vector<Request*> reqs;
+    int64_t G = 0, N = 0, NNZ = 0;
+    int64_t* h_vo = nullptr;
+    int64_t* h_rp = nullptr;
+    int32_t* h_col = nullptr;
+    int64_t* h_tot = nullptr;
+    int64_t* h_pv = nullptr;
+    unsigned long long* d_tot = nullptr;
+    unsigned long long* d_pv = nullptr;
+};
+
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     Request* req = nullptr;
+    BatchJob job;                // job.reqs non-empty: the slot runs a fused batch
     tc_ocsr* o = nullptr;
     bool o_cached = false;       // o belongs to the resident cache
     unsigned long long* d_total = nullptr;
@@ -73,7 +93,7 @@ int64_t estimate_bytes(int64_t n, int64_t nnz, const tc::Tuning& t) {
     const int64_t dmax = std::max<int64_t>(1, (int64_t)std::sqrt((double)(2 * m)) + 1);
     const int64_t iw = std::min(n, m) + m / t.chunk + 2;
     const int64_t ic = dmax * m / ((int64_t)t.table_cap * t.chunk) + m / t.table_cap + m / t.chunk + m / (t.warp_max + 1) + 6;
-    const int64_t ocsr = 16 * (n + 1) + 4 * (2 * m + n) + 16 * (iw + ic);
+    const int64_t ocsr = 16 * (n + 1) + 4 * (3 * m + 9 * n) + 16 * (iw + ic);
     const int64_t input = 8 * (n + 1) + 4 * nnz;
     const int64_t scratch = 8 * n + 64 * 1024 + 8 * (n + 1);  // deg, pc, scan tiles, outputs
     return ocsr + input + scratch + (1 << 20);
@@ -220,6 +240,111 @@ struct tc_server {
         return true;
     }
 
+    bool fusable(const Request* r) const {
+        return r->csr && !(r->flags & TC_VALIDATE) && r->nnz <= cfg.batch_nnz && r->h_rp[0] == 0 &&
+               r->h_rp[r->n] == r->nnz;
+    }
+
+    void free_job(BatchJob& b, cudaStream_t s) {
+        pin_free(b.h_vo, sizeof(int64_t) * (b.G + 1));
+        pin_free(b.h_rp, sizeof(int64_t) * (b.N + 1));
+        pin_free(b.h_col, sizeof(int32_t) * std::max<int64_t>(b.NNZ, 1));
+        pin_free(b.h_tot, sizeof(int64_t) * std::max<int64_t>(b.G, 1));
+        if (b.h_pv) pin_free(b.h_pv, sizeof(int64_t) * std::max<int64_t>(b.N, 1));
+        tc::dev_free(b.d_tot, s);
+        tc::dev_free(b.d_pv, s);
+        b = BatchJob();
+    }
+
+    // Concatenate the requests' CSRs and run the batched build + count.
+    bool launch_batch(Slot& sl, std::vector<Request*>& B) {
+        cudaStream_t s = sl.stream;
+        BatchJob& b = sl.job;
+        b.G = (int64_t)B.size();
+        for (Request* r : B) {
+            b.N += r->n;
+            b.NNZ += r->nnz;
+        }
+        b.h_vo = (int64_t*)pin_alloc(sizeof(int64_t) * (b.G + 1));
+        b.h_rp = (int64_t*)pin_alloc(sizeof(int64_t) * (b.N + 1));
+        b.h_col = (int32_t*)pin_alloc(sizeof(int32_t) * std::max<int64_t>(b.NNZ, 1));
+        b.h_tot = (int64_t*)pin_alloc(sizeof(int64_t) * std::max<int64_t>(b.G, 1));
+        if (cfg.per_vertex) b.h_pv = (int64_t*)pin_alloc(sizeof(int64_t) * std::max<int64_t>(b.N, 1));
+        tc_status st = (b.h_vo && b.h_rp && b.h_col && b.h_tot && (!cfg.per_vertex || b.h_pv)) ? TC_OK : TC_ERR_OOM;
+        int64_t *d_vo = nullptr, *d_rp = nullptr;
+        int32_t* d_col = nullptr;
+        tc_ocsr* o = nullptr;
+        if (st == TC_OK) {
+            int64_t vo = 0, eo = 0;
+            for (int64_t i = 0; i < b.G; ++i) {
+                const Request* r = B[i];
+                b.h_vo[i] = vo;
+                for (int64_t v = 0; v < r->n; ++v) b.h_rp[vo + v] = eo + r->h_rp[v];
+                if (r->nnz) std::memcpy(b.h_col + eo, r->h_a, sizeof(int32_t) * r->nnz);
+                vo += r->n;
+                eo += r->nnz;
+            }
+            b.h_vo[b.G] = vo;
+            b.h_rp[b.N] = eo;
+            cudaError_t e = tc::dev_alloc((void**)&d_vo, sizeof(int64_t) * (b.G + 1), s);
+            if (e == cudaSuccess) e = tc::dev_alloc((void**)&d_rp, sizeof(int64_t) * (b.N + 1), s);
+            if (e == cudaSuccess) e = tc::dev_alloc((void**)&d_col, sizeof(int32_t) * std::max<int64_t>(b.NNZ, 1), s);
+            if (e == cudaSuccess) e = tc::dev_alloc((void**)&b.d_tot, sizeof(int64_t) * b.G, s);
+            if (e == cudaSuccess && cfg.per_vertex)
+                e = tc::dev_alloc((void**)&b.d_pv, sizeof(int64_t) * std::max<int64_t>(b.N, 1), s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_vo, b.h_vo, sizeof(int64_t) * (b.G + 1), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, b.h_rp, sizeof(int64_t) * (b.N + 1), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && b.NNZ)
+                e = cudaMemcpyAsync(d_col, b.h_col, sizeof(int32_t) * b.NNZ, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) st = TC_ERR_OOM;
+        }
+        if (st == TC_OK) st = tc::build_from_device_csr(ctx, b.N, b.NNZ, d_rp, d_col, d_vo, b.G, false, &o, s);
+        tc::dev_free(d_vo, s);
+        tc::dev_free(d_rp, s);
+        tc::dev_free(d_col, s);
+        if (st == TC_OK) st = tc::count_device(ctx, o, b.d_tot, cfg.per_vertex ? b.d_pv : nullptr, s);
+        if (st == TC_OK) {
+            cudaMemcpyAsync(b.h_tot, b.d_tot, sizeof(int64_t) * b.G, cudaMemcpyDeviceToHost, s);
+            if (cfg.per_vertex && b.N > 0)
+                cudaMemcpyAsync(b.h_pv, b.d_pv, sizeof(int64_t) * b.N, cudaMemcpyDeviceToHost, s);
+            cudaEventRecord(sl.ev, s);
+        }
+        if (st != TC_OK) {
+            if (o) tc_ocsr_release(o, s);
+            free_job(b, s);
+            for (Request* r : B) {
+                inflight -= r->est_bytes;
+                free_inputs(r);
+                finish(r, st);
+            }
+            return false;
+        }
+        b.reqs = B;
+        sl.o = o;
+        stats.batches++;
+        stats.batched_requests += b.G;
+        return true;
+    }
+
+    void retire_batch(Slot& sl) {
+        BatchJob& b = sl.job;
+        for (int64_t i = 0; i < b.G; ++i) {
+            Request* r = b.reqs[i];
+            r->total = b.h_tot[i];
+            if (cfg.per_vertex) r->pv.assign(b.h_pv + b.h_vo[i], b.h_pv + b.h_vo[i + 1]);
+            pin_free(r->h_total, sizeof(int64_t));
+            if (r->h_pv) pin_free(r->h_pv, sizeof(int64_t) * std::max<int64_t>(r->n, 1));
+            r->h_total = nullptr;
+            r->h_pv = nullptr;
+            free_inputs(r);
+            inflight -= r->est_bytes;
+            finish(r, TC_OK);
+        }
+        tc_ocsr_release(sl.o, sl.stream);
+        sl.o = nullptr;
+        free_job(b, sl.stream);
+    }
+
     void retire(Slot& sl) {
         Request* r = sl.req;
         r->total = *r->h_total;
@@ -256,8 +381,10 @@ struct tc_server {
         while (true) {
             bool progressed = false;
             for (auto& sl : slots) {
-                if (sl.req && cudaEventQuery(sl.ev) == cudaSuccess) {
-                    retire(sl);
+                const bool busy = sl.req || !sl.job.reqs.empty();
+                if (busy && cudaEventQuery(sl.ev) == cudaSuccess) {
+                    if (sl.req) retire(sl);
+                    else retire_batch(sl);
                     progressed = true;
                 }
             }
@@ -265,10 +392,42 @@ struct tc_server {
             while (!queue.empty()) {
                 Slot* free_slot = nullptr;
                 for (auto& sl : slots)
-                    if (!sl.req) { free_slot = &sl; break; }
+                    if (!sl.req && sl.job.reqs.empty()) { free_slot = &sl; break; }
                 if (!free_slot) break;
                 Request* r = queue.front();
                 const bool hit = r->key && cache.count(r->key);
+                // fuse the small requests waiting together at the head of the queue
+                if (!hit && cfg.batch_graphs > 1 && queue.size() >= 2 && fusable(r)) {
+                    std::vector<Request*> B;
+                    int64_t need = 0, nnz = 0;
+                    for (Request* q : queue) {
+                        if ((int)B.size() >= cfg.batch_graphs || !fusable(q) || (q->key && cache.count(q->key)) ||
+                            nnz + q->nnz > 8 * cfg.batch_nnz)
+                            break;
+                        B.push_back(q);
+                        need += q->est_bytes;
+                        nnz += q->nnz;
+                    }
+                    if (B.size() >= 2) {
+                        if (resident + inflight + need > cfg.hbm_budget_bytes) evict_until(need);
+                        if (resident + inflight + need <= cfg.hbm_budget_bytes) {
+                            const auto now = Clock::now();
+                            for (Request* q : B) {
+                                queue.pop_front();
+                                q->t_admit = now;
+                            }
+                            inflight += need;
+                            stats.admitted += (int64_t)B.size();
+                            stats.peak_inflight_bytes = std::max(stats.peak_inflight_bytes, inflight);
+                            launch_batch(*free_slot, B);
+                            int busy = 0;
+                            for (auto& sl : slots) busy += (sl.req || !sl.job.reqs.empty()) ? 1 : 0;
+                            stats.peak_inflight = std::max(stats.peak_inflight, busy);
+                            progressed = true;
+                            continue;
+                        }
+                    }
+                }
                 const int64_t need = hit ? 0 : r->est_bytes;
                 if (resident + inflight + need > cfg.hbm_budget_bytes) evict_until(need);
                 if (resident + inflight + need > cfg.hbm_budget_bytes) {
@@ -289,14 +448,14 @@ struct tc_server {
                 stats.peak_inflight_bytes = std::max(stats.peak_inflight_bytes, inflight);
                 launch(*free_slot, r);
                 int busy = 0;
-                for (auto& sl : slots) busy += sl.req != nullptr;
+                for (auto& sl : slots) busy += (sl.req || !sl.job.reqs.empty()) ? 1 : 0;
                 stats.peak_inflight = std::max(stats.peak_inflight, busy);
                 progressed = true;
             }
             stats.resident_bytes = resident;
             if (progressed) cv_done.notify_all();
             bool any_busy = false;
-            for (auto& sl : slots) any_busy |= sl.req != nullptr;
+            for (auto& sl : slots) any_busy |= sl.req != nullptr || !sl.job.reqs.empty();
             if (stop && queue.empty() && !any_busy) break;
             if (!progressed) {
                 if (any_busy) cv_work.wait_for(lk, std::chrono::microseconds(20));
@@ -316,6 +475,8 @@ tc_status tc_server_create(const tc_server_config* cfg, const tc_config* tuning,
     if (s->cfg.slots <= 0) s->cfg.slots = 8;
     if (s->cfg.slots > 64) s->cfg.slots = 64;
     if (s->cfg.hbm_budget_bytes <= 0) s->cfg.hbm_budget_bytes = 40ll << 30;
+    if (s->cfg.batch_graphs <= 0) s->cfg.batch_graphs = 32;
+    if (s->cfg.batch_nnz <= 0) s->cfg.batch_nnz = 1ll << 20;
     tc_status st = tc_ctx_create(s->cfg.device, tuning, &s->ctx);
     if (st != TC_OK) {
         delete s;

@@ -109,19 +109,42 @@ def test_server_mix_equals_alone(B):
         tk = srv.submit(g.n, g.row_ptr, g.col)
         alone.append(srv.wait(tk, 60000))
     srv.close()
-    # mixed: 8 slots, all submitted at once, some repeated keys
-    srv = B.Server(slots=8, per_vertex=True)
-    tickets = [srv.submit(g.n, g.row_ptr, g.col, key=1000 + (i % 12)) for i, g in enumerate(graphs[:12])]
-    tickets += [srv.submit(g.n, g.row_ptr, g.col) for g in graphs[12:]]
-    mixed = [srv.wait(tk, 60000) for tk in tickets]
+    # mixed: 8 slots, all submitted at once, some repeated keys; once with every
+    # request on its own slot, once with small requests fused into batches
+    for fuse in (1, 32):
+        srv = B.Server(slots=8, per_vertex=True, batch_graphs=fuse)
+        tickets = [srv.submit(g.n, g.row_ptr, g.col, key=1000 + (i % 12)) for i, g in enumerate(graphs[:12])]
+        tickets += [srv.submit(g.n, g.row_ptr, g.col) for g in graphs[12:]]
+        mixed = [srv.wait(tk, 60000) for tk in tickets]
+        st = srv.stats()
+        srv.close()
+        for (T, t), a, m in zip(expect, alone, mixed):
+            assert a["status"] == 0 and m["status"] == 0
+            assert a["total"] == T == m["total"]
+            np.testing.assert_array_equal(a["per_vertex"], t)
+            np.testing.assert_array_equal(m["per_vertex"], t)
+        assert st["finished"] == len(graphs)
+        if fuse == 1:
+            assert st["peak_inflight"] >= 2 and st["batches"] == 0
+
+
+def test_server_fuses_small_requests(B):
+    """Small requests queued together run as fused batches; every result stays
+    exact, including graphs without edges and a repeated graph."""
+    graphs = serving_mix(30, seed=4) + [gen.from_pairs(7, [], []), gen.from_pairs(1, [], [])]
+    graphs.append(graphs[0])
+    # a larger request first holds the only slot while the small ones queue up
+    graphs.insert(0, gen.rmat(17, 16, seed=2))
+    expect = [oracle.count(g.n, g.row_ptr, g.col) for g in graphs]
+    srv = B.Server(slots=1, per_vertex=True, batch_graphs=8, batch_nnz=1 << 19)
+    tickets = [srv.submit(g.n, g.row_ptr, g.col) for g in graphs]
+    res = [srv.wait(tk, 60000) for tk in tickets]
     st = srv.stats()
     srv.close()
-    for (T, t), a, m in zip(expect, alone, mixed):
-        assert a["status"] == 0 and m["status"] == 0
-        assert a["total"] == T == m["total"]
-        np.testing.assert_array_equal(a["per_vertex"], t)
-        np.testing.assert_array_equal(m["per_vertex"], t)
-    assert st["finished"] == len(graphs) and st["peak_inflight"] >= 2
+    for (T, t), r in zip(expect, res):
+        assert r["status"] == 0 and r["total"] == T
+        np.testing.assert_array_equal(r["per_vertex"], t)
+    assert st["batches"] >= 2 and st["finished"] == len(graphs)
 
 
 def test_server_cache_hits_and_edge_lists(B):

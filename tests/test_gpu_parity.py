@@ -146,7 +146,7 @@ def test_complete_graph(ctx, n):
 
 
 def test_wheels_and_friendship(ctx):
-    for k in (4, 50, 3000):
+    for k in (4, 50, 3000, 10000):
         rim = [(1 + i, 1 + (i + 1) % k) for i in range(k)]
         g = graph_from_edges(k + 1, rim + [(0, 1 + i) for i in range(k)])
         T, t = gpu_count(ctx, g)
