@@ -55,19 +55,28 @@ struct Request {
     bool done = false;
 };
 
-// A fused batch of small requests on one slot: pinned concatenated inputs and
-// outputs, and the device copies (stream-ordered allocations).
+// A fused batch of small requests on one slot: pinned offsets and outputs,
+// and device outputs (stream-ordered allocations).  The requests' own pinned
+// inputs are copied straight into the concatenated device arrays.
 struct BatchJob {
     std::vector<Request*> reqs;
     int64_t G = 0, N = 0, NNZ = 0;
-    int64_t* h_vo = nullptr;
-    int64_t* h_rp = nullptr;
-    int32_t* h_col = nullptr;
+    int64_t* h_off = nullptr;    // [2(G+1)]: vertex offsets, then edge offsets
     int64_t* h_tot = nullptr;
     int64_t* h_pv = nullptr;
     unsigned long long* d_tot = nullptr;
     unsigned long long* d_pv = nullptr;
 };
+
+// The row offsets of graph g were copied as its own (starting at 0): shift
+// them by the graph's first edge, and close the concatenated array.
+__global__ void k_shift_rows(int64_t G, const int64_t* __restrict__ off, int64_t* __restrict__ rp) {
+    const int64_t* vo = off;
+    const int64_t* eo = off + G + 1;
+    for (int64_t g = blockIdx.x; g < G; g += gridDim.x)
+        for (int64_t v = vo[g] + threadIdx.x; v < vo[g + 1]; v += blockDim.x) rp[v] += eo[g];
+    if (blockIdx.x == 0 && threadIdx.x == 0) rp[vo[G]] = eo[G];
+}
 
 struct Slot {
     cudaStream_t stream = nullptr;
@@ -246,9 +255,7 @@ struct tc_server {
     }
 
     void free_job(BatchJob& b, cudaStream_t s) {
-        pin_free(b.h_vo, sizeof(int64_t) * (b.G + 1));
-        pin_free(b.h_rp, sizeof(int64_t) * (b.N + 1));
-        pin_free(b.h_col, sizeof(int32_t) * std::max<int64_t>(b.NNZ, 1));
+        pin_free(b.h_off, sizeof(int64_t) * 2 * (b.G + 1));
         pin_free(b.h_tot, sizeof(int64_t) * std::max<int64_t>(b.G, 1));
         if (b.h_pv) pin_free(b.h_pv, sizeof(int64_t) * std::max<int64_t>(b.N, 1));
         tc::dev_free(b.d_tot, s);
@@ -256,7 +263,7 @@ struct tc_server {
         b = BatchJob();
     }
 
-    // Concatenate the requests' CSRs and run the batched build + count.
+    // Concatenate the requests' CSRs on the device and run the batched build + count.
     bool launch_batch(Slot& sl, std::vector<Request*>& B) {
         cudaStream_t s = sl.stream;
         BatchJob& b = sl.job;
@@ -265,41 +272,44 @@ struct tc_server {
             b.N += r->n;
             b.NNZ += r->nnz;
         }
-        b.h_vo = (int64_t*)pin_alloc(sizeof(int64_t) * (b.G + 1));
-        b.h_rp = (int64_t*)pin_alloc(sizeof(int64_t) * (b.N + 1));
-        b.h_col = (int32_t*)pin_alloc(sizeof(int32_t) * std::max<int64_t>(b.NNZ, 1));
+        b.h_off = (int64_t*)pin_alloc(sizeof(int64_t) * 2 * (b.G + 1));
         b.h_tot = (int64_t*)pin_alloc(sizeof(int64_t) * std::max<int64_t>(b.G, 1));
         if (cfg.per_vertex) b.h_pv = (int64_t*)pin_alloc(sizeof(int64_t) * std::max<int64_t>(b.N, 1));
-        tc_status st = (b.h_vo && b.h_rp && b.h_col && b.h_tot && (!cfg.per_vertex || b.h_pv)) ? TC_OK : TC_ERR_OOM;
-        int64_t *d_vo = nullptr, *d_rp = nullptr;
+        tc_status st = (b.h_off && b.h_tot && (!cfg.per_vertex || b.h_pv)) ? TC_OK : TC_ERR_OOM;
+        int64_t *d_off = nullptr, *d_rp = nullptr;
         int32_t* d_col = nullptr;
         tc_ocsr* o = nullptr;
         if (st == TC_OK) {
-            int64_t vo = 0, eo = 0;
+            int64_t* vo = b.h_off;
+            int64_t* eo = b.h_off + b.G + 1;
+            vo[0] = eo[0] = 0;
             for (int64_t i = 0; i < b.G; ++i) {
-                const Request* r = B[i];
-                b.h_vo[i] = vo;
-                for (int64_t v = 0; v < r->n; ++v) b.h_rp[vo + v] = eo + r->h_rp[v];
-                if (r->nnz) std::memcpy(b.h_col + eo, r->h_a, sizeof(int32_t) * r->nnz);
-                vo += r->n;
-                eo += r->nnz;
+                vo[i + 1] = vo[i] + B[i]->n;
+                eo[i + 1] = eo[i] + B[i]->nnz;
             }
-            b.h_vo[b.G] = vo;
-            b.h_rp[b.N] = eo;
-            cudaError_t e = tc::dev_alloc((void**)&d_vo, sizeof(int64_t) * (b.G + 1), s);
+            cudaError_t e = tc::dev_alloc((void**)&d_off, sizeof(int64_t) * 2 * (b.G + 1), s);
             if (e == cudaSuccess) e = tc::dev_alloc((void**)&d_rp, sizeof(int64_t) * (b.N + 1), s);
             if (e == cudaSuccess) e = tc::dev_alloc((void**)&d_col, sizeof(int32_t) * std::max<int64_t>(b.NNZ, 1), s);
             if (e == cudaSuccess) e = tc::dev_alloc((void**)&b.d_tot, sizeof(int64_t) * b.G, s);
             if (e == cudaSuccess && cfg.per_vertex)
                 e = tc::dev_alloc((void**)&b.d_pv, sizeof(int64_t) * std::max<int64_t>(b.N, 1), s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_vo, b.h_vo, sizeof(int64_t) * (b.G + 1), cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, b.h_rp, sizeof(int64_t) * (b.N + 1), cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess && b.NNZ)
-                e = cudaMemcpyAsync(d_col, b.h_col, sizeof(int32_t) * b.NNZ, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_off, b.h_off, sizeof(int64_t) * 2 * (b.G + 1), cudaMemcpyHostToDevice, s);
+            for (int64_t i = 0; i < b.G && e == cudaSuccess; ++i) {
+                const Request* r = B[i];
+                if (r->n) e = cudaMemcpyAsync(d_rp + vo[i], r->h_rp, sizeof(int64_t) * r->n, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess && r->nnz)
+                    e = cudaMemcpyAsync(d_col + eo[i], r->h_a, sizeof(int32_t) * r->nnz, cudaMemcpyHostToDevice, s);
+            }
+            if (e == cudaSuccess) {
+                k_shift_rows<<<(unsigned)std::min<int64_t>(b.G, 1024), 256, 0, s>>>(b.G, d_off, d_rp);
+                e = cudaGetLastError();
+            }
             if (e != cudaSuccess) st = TC_ERR_OOM;
         }
+        int64_t* d_vo = d_off;  // the vertex offsets lead the offset array
         if (st == TC_OK) st = tc::build_from_device_csr(ctx, b.N, b.NNZ, d_rp, d_col, d_vo, b.G, false, &o, s);
-        tc::dev_free(d_vo, s);
+        tc::dev_free(d_off, s);
         tc::dev_free(d_rp, s);
         tc::dev_free(d_col, s);
         if (st == TC_OK) st = tc::count_device(ctx, o, b.d_tot, cfg.per_vertex ? b.d_pv : nullptr, s);
@@ -331,7 +341,7 @@ struct tc_server {
         for (int64_t i = 0; i < b.G; ++i) {
             Request* r = b.reqs[i];
             r->total = b.h_tot[i];
-            if (cfg.per_vertex) r->pv.assign(b.h_pv + b.h_vo[i], b.h_pv + b.h_vo[i + 1]);
+            if (cfg.per_vertex) r->pv.assign(b.h_pv + b.h_off[i], b.h_pv + b.h_off[i + 1]);
             pin_free(r->h_total, sizeof(int64_t));
             if (r->h_pv) pin_free(r->h_pv, sizeof(int64_t) * std::max<int64_t>(r->n, 1));
             r->h_total = nullptr;
