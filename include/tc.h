@@ -108,7 +108,7 @@ typedef struct tc_ocsr tc_ocsr;
 enum {
     TC_PH_DEGREE = 0, TC_PH_VALIDATE, TC_PH_ORIENT_COUNT, TC_PH_ORIENT_SCAN, TC_PH_ORIENT_SCATTER,
     TC_PH_PIVOT_COUNT, TC_PH_PIVOT_SCAN, TC_PH_PIVOT_SCATTER, TC_PH_ITEMS, TC_PH_COUNT_SMALL,
-    TC_PH_COUNT_WARP, TC_PH_COUNT_CTA, TC_PH_EDGE_SORT, TC_PH_COUNT_INIT, TC_PH_RANK, TC_PH_RELABEL
+    TC_PH_COUNT_WARP, TC_PH_COUNT_CTA, TC_PH_EDGE_SORT, TC_PH_COUNT_INIT, TC_PH_RANK, TC_PH_ROW_SORT
 };
 typedef struct tc_trace {
     int64_t launches;                        /* kernel launches since the last read */

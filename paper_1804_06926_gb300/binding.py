@@ -64,7 +64,7 @@ class tc_result(C.Structure):
 
 TRACE_PHASES = ("degree", "validate", "orient_count", "orient_scan", "orient_scatter", "pivot_count",
                 "pivot_scan", "pivot_scatter", "items", "count_small", "count_warp", "count_cta", "edge_sort",
-                "count_init", "rank", "relabel")
+                "count_init", "rank", "row_sort")
 
 
 class tc_trace(C.Structure):

@@ -466,6 +466,67 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
 }
 
 
+// Partition the colr rows with kSortedMin <= d+ <= kSortedMax into buckets of
+// descending rank_level(n - x) (see tc_internal.cuh): one warp per row, the
+// row staged in the warp's shared-memory buffer, a histogram of levels, their
+// exclusive prefix in descending order, and an atomic scatter back.
+constexpr int kSortWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const int64_t* __restrict__ rpp,
+                                                               const int32_t* __restrict__ dplus,
+                                                               int32_t* __restrict__ colr) {
+    extern __shared__ int sbuf[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int* buf = sbuf + w * (kSortedMax + kRankLevels);
+    int* cur = buf + kSortedMax;  // per level: count, then next free position
+    const int64_t nwarps = (int64_t)gridDim.x * kSortWarps;
+    for (int64_t u0 = ((int64_t)blockIdx.x * kSortWarps + w) * 32; u0 < n; u0 += nwarps * 32) {
+        const int64_t ul = u0 + lane;
+        const int dl = ul < n ? dplus[ul] : 0;
+        unsigned todo = __ballot_sync(0xffffffffu, dl >= kSortedMin && dl <= kSortedMax);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t u = u0 + src;
+            const int d = __shfl_sync(0xffffffffu, dl, src);
+            int32_t* row = colr + colr_row(rpp, u);
+            for (int i = lane; i < kRankLevels; i += 32) cur[i] = 0;
+            __syncwarp();
+            for (int i = lane; i < d; i += 32) {
+                const int x = row[i];
+                buf[i] = x;
+                atomicAdd(&cur[rank_level((unsigned)(n - x))], 1);
+            }
+            __syncwarp();
+            // exclusive prefix over levels kRankLevels-1 .. 0 (lane l: 8 levels)
+            int c[8], t = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                c[j] = cur[kRankLevels - 1 - (lane * 8 + j)];
+                t += c[j];
+            }
+            int inc = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            int run = inc - t;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                cur[kRankLevels - 1 - (lane * 8 + j)] = run;
+                run += c[j];
+            }
+            __syncwarp();
+            for (int i = lane; i < d; i += 32) {
+                const int x = buf[i];
+                row[atomicAdd(&cur[rank_level((unsigned)(n - x))], 1)] = x;
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // ============================================================================
 // a-4  partition (Alg. 2 Partition; Sec. 4.2.2 dynamic grouping).
 // Every oriented edge (u, v) with a = d+(u), b = d+(v) falls in one class:
@@ -819,6 +880,15 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
             else k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
             TC_LAUNCH(ctx);
         }
+    }
+    // colr rows of the partners whose lists the count kernels stream, sorted by rank
+    if (n > 0) {
+        PhaseScope ph(ctx, kPhRowSort, s);
+        const size_t sm = sizeof(int) * (kSortedMax + kRankLevels) * kSortWarps;
+        cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const unsigned sg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kSortWarps - 1) / (32 * kSortWarps), (int64_t)ns * 8));
+        k_sort_rows<<<sg, 32 * kSortWarps, sm, s>>>(n, o->rpp, o->dplus, o->colr);
+        TC_LAUNCH(ctx);
     }
     // a-4: classify, group oriented edges by pivot
     {

@@ -23,6 +23,7 @@
 // the table slot and is flushed once per item; q gets one atomic per partner
 // with a non-zero count; p one atomic per item.
 #include <algorithm>
+#include <climits>
 
 #include "tc_internal.cuh"
 
@@ -211,6 +212,7 @@ struct Table {
     unsigned short* cell;  // direct mode
     unsigned* cell32;      // direct mode, 32-bit cells
     int lo, span;
+    int lev;               // rank_level(n - smallest key): where walks of partitioned lists may stop
 };
 
 // Probe x; on a hit count it (per-vertex counter of x when PV) and return
@@ -486,24 +488,31 @@ __device__ __forceinline__ int probe1(const Table& t, int x) {
 }
 
 // probe_list for the padded rank-id rows: the list starts 16-byte aligned and
-// its last vector is filled up with -1, so every vector is probed whole.
+// its last vector is filled up with -1, so every vector is probed whole.  The
+// lane walks vectors nv-1-r, nv-1-r-G, ... (top down).  For a list partitioned
+// by rank level, lev_exit is the level of the table's smallest key and the
+// walk stops after a batch whose lowest vector lies wholly in higher levels
+// (everything further down is below the table); lev_exit = INT_MAX walks the
+// whole list.
 template <int MODE, bool PV>
 __device__ __forceinline__ int probe_list_padded(const Table& tb, const int32_t* __restrict__ L, int64_t qb, int dq,
-                                                 int r, int G) {
+                                                 int r, int G, int lev_exit, unsigned n) {
     const int4* __restrict__ lv = reinterpret_cast<const int4*>(L + qb);
     const int nv = (dq + 3) >> 2;
     int myc = 0;
-    for (int v0 = r; v0 < nv; v0 += G * kVec) {
+    for (int v0 = nv - 1 - r; v0 >= 0; v0 -= G * kVec) {
         int4 w[kVec];
 #pragma unroll
         for (int u = 0; u < kVec; ++u) {
-            const int vv = v0 + u * G;
-            w[u] = vv < nv ? lv[vv] : make_int4(-1, -1, -1, -1);
+            const int vv = v0 - u * G;
+            w[u] = vv >= 0 ? lv[vv] : make_int4(-1, -1, -1, -1);
         }
 #pragma unroll
         for (int u = 0; u < kVec; ++u)
             myc += probe1<MODE, PV>(tb, w[u].x) + probe1<MODE, PV>(tb, w[u].y) + probe1<MODE, PV>(tb, w[u].z) +
                    probe1<MODE, PV>(tb, w[u].w);
+        const int4 t = w[kVec - 1];
+        if (rank_level(n - (unsigned)max(max(t.x, t.y), max(t.z, t.w))) > lev_exit) break;
     }
     return myc;
 }
@@ -586,8 +595,10 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             const bool valid = i < sc.coff[c] + sc.ccnt[c];
             const int dq = valid ? sc.dq[i] : 0;
             const int64_t qb = valid ? sc.qb[i] : 0;
+            // level-partitioned lists (kSortedMin <= d+ <= kSortedMax) may stop below the table
+            const int lev_exit = (dq >= kSortedMin && dq <= kSortedMax) ? tb.lev : INT_MAX;
             int myc = MODE == kModeBsearch ? probe_list<MODE, PV>(tb, L, qb, dq, r, G)
-                                           : probe_list_padded<MODE, PV>(tb, L, qb, dq, r, G);
+                                           : probe_list_padded<MODE, PV>(tb, L, qb, dq, r, G, lev_exit, (unsigned)a.n);
             for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
             if (r == 0 && valid && myc) {
                 acc += (unsigned long long)myc;
@@ -691,6 +702,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
         const int len = (int)min((int64_t)a.cap, r1 - lb);
         Table tb{};
         tb.len = len;
+        tb.lev = INT_MAX;
         int mode = PROBE == kProbeHash ? kModeHash : kModeBsearch;
         if (PROBE == kProbeHash && a.bitmap_bits > 0) {
             int mn, mx;
@@ -721,6 +733,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
                 tb.lo = mn;
                 tb.span = mx - mn + 1;
             }
+            if (mx >= 0) tb.lev = rank_level((unsigned)(a.n - mn));
         }
         // the table region is all zeros here: every item resets what it set
         int nflush = 0;

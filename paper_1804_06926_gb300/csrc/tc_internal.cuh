@@ -51,6 +51,21 @@ namespace tc {
 __host__ __device__ __forceinline__ int64_t colr_row(const int64_t* rpp, int64_t u) {
     return (rpp[u] + 3 * u + 3) & ~(int64_t)3;
 }
+// colr rows with kSortedMin <= d+(u) <= kSortedMax are partitioned by the
+// level of each rank id x, rank_level(n - x) (an eighth of an octave of the
+// distance to the top rank: non-increasing in x), into buckets of descending
+// level, i.e. ascending x from bucket to bucket (unordered inside a bucket).
+// A count kernel walking such a list from the top may stop at a vector whose
+// elements all lie in levels above that of a table's smallest key: every
+// element before it is then below that key.  Other rows keep vertex-id order.
+constexpr int kSortedMin = 64;
+constexpr int kSortedMax = 2048;
+constexpr int kRankLevels = 256;  // 32 octaves x 8
+__device__ __forceinline__ int rank_level(unsigned y) {  // 1 <= y < 2^32
+    const int e = 31 - __clz(y);
+    const unsigned sub = e >= 3 ? (y >> (e - 3)) & 7u : (y << (3 - e)) & 7u;
+    return e * 8 + (int)sub;
+}
 }  // namespace tc
 
 // Library-owned oriented CSR and its work partition.
@@ -97,7 +112,7 @@ namespace tc {
 enum Phase {
     kPhDegree = 0, kPhValidate, kPhOrientCount, kPhOrientScan, kPhOrientScatter, kPhPivotCount, kPhPivotScan,
     kPhPivotScatter, kPhItems, kPhCountSmall, kPhCountWarp, kPhCountCta, kPhEdgeSort, kPhCountInit, kPhRank,
-    kPhRelabel, kNumPhases
+    kPhRowSort, kNumPhases
 };
 
 // RAII phase marker: records an event pair on `s` when tracing is on.
