@@ -470,7 +470,10 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
 // descending rank_level(n - x) (see tc_internal.cuh): one warp per row, the
 // row staged in the warp's shared-memory buffer, a histogram of levels, their
 // exclusive prefix in descending order, and an atomic scatter back.
-constexpr int kSortWarps = 4;
+#ifndef TC_SORT_WARPS
+#define TC_SORT_WARPS 4
+#endif
+constexpr int kSortWarps = TC_SORT_WARPS;
 
 __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const int64_t* __restrict__ rpp,
                                                                const int32_t* __restrict__ dplus,
@@ -886,7 +889,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         PhaseScope ph(ctx, kPhRowSort, s);
         const size_t sm = sizeof(int) * (kSortedMax + kRankLevels) * kSortWarps;
         cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        const unsigned sg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kSortWarps - 1) / (32 * kSortWarps), (int64_t)ns * 8));
+        const unsigned sg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kSortWarps - 1) / (32 * kSortWarps), (int64_t)ns * 32 / kSortWarps));
         k_sort_rows<<<sg, 32 * kSortWarps, sm, s>>>(n, o->rpp, o->dplus, o->colr);
         TC_LAUNCH(ctx);
     }

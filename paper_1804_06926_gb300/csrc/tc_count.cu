@@ -332,7 +332,10 @@ __device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, 
 // warp_partners), and each lane probes the 4 elements of its vector in the
 // zero-encoded hash table of the pivot (padding -1 never hits).  Per-partner
 // hit counts come from one ballot per vector component.
-constexpr int kWarpVec = 2;
+#ifndef TC_WARP_VEC
+#define TC_WARP_VEC 2
+#endif
+constexpr int kWarpVec = TC_WARP_VEC;
 
 template <bool PV>
 __device__ __forceinline__ unsigned long long warp_partners_vec(const CountArgs& a, const int* keys, int* cnts,
@@ -342,12 +345,28 @@ __device__ __forceinline__ unsigned long long warp_partners_vec(const CountArgs&
     const unsigned le_mask = lane == 31 ? FULL : ((2u << lane) - 1u);
     const int4* __restrict__ lv = reinterpret_cast<const int4*>(a.colr);
     unsigned long long acc = 0;
+    // partner descriptors of the next group of 32 are loaded one group ahead
+    int qn = 0, nvn = 0;
+    int64_t qvn = 0;
+    if (pb + lane < pe) {
+        qn = a.pcol[pbase + pb + lane];
+        qvn = colr_row(a.rpp, qn) >> 2;
+        nvn = (a.dp[qn] + 3) >> 2;
+    }
     for (int g0 = pb; g0 < pe; g0 += 32) {
-        const int i = g0 + lane;
-        const bool valid = i < pe;
-        const int q = valid ? a.pcol[pbase + i] : 0;
-        const int64_t qv = valid ? (colr_row(a.rpp, q) >> 2) : 0;   // first vector of q's row
-        const int nvq = valid ? (a.dp[q] + 3) >> 2 : 0;   // >= 1: partner lists are non-empty
+        const bool valid = g0 + lane < pe;
+        const int q = qn;
+        const int64_t qv = qvn;  // first vector of q's row
+        const int nvq = nvn;     // >= 1: partner lists are non-empty
+        if (g0 + 32 + lane < pe) {
+            qn = a.pcol[pbase + g0 + 32 + lane];
+            qvn = colr_row(a.rpp, qn) >> 2;
+            nvn = (a.dp[qn] + 3) >> 2;
+        } else {  // past the last partner: an empty descriptor
+            qn = 0;
+            qvn = 0;
+            nvn = 0;
+        }
         const int incl = warp_incl_scan_i(nvq);
         const int tot = __shfl_sync(FULL, incl, 31);
         const int excl = incl - nvq;
@@ -860,8 +879,11 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
 // ---------------------------------------------------------------------------
 // warp-table kernel: each warp owns a table of 2*wcap slots
 // ---------------------------------------------------------------------------
+#ifndef TC_WARP_MIN_BLOCKS
+#define TC_WARP_MIN_BLOCKS 4
+#endif
 template <bool PV, int PROBE>
-__global__ void __launch_bounds__(256) k_count_warp(CountArgs a, int wcap) {
+__global__ void __launch_bounds__(256, TC_WARP_MIN_BLOCKS) k_count_warp(CountArgs a, int wcap) {
     extern __shared__ int smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per_warp = 8 * wcap;

@@ -58,7 +58,10 @@ __host__ __device__ __forceinline__ int64_t colr_row(const int64_t* rpp, int64_t
 // A count kernel walking such a list from the top may stop at a vector whose
 // elements all lie in levels above that of a table's smallest key: every
 // element before it is then below that key.  Other rows keep vertex-id order.
-constexpr int kSortedMin = 64;
+#ifndef TC_SORTED_MIN
+#define TC_SORTED_MIN 64
+#endif
+constexpr int kSortedMin = TC_SORTED_MIN;
 constexpr int kSortedMax = 2048;
 constexpr int kRankLevels = 256;  // 32 octaves x 8
 __device__ __forceinline__ int rank_level(unsigned y) {  // 1 <= y < 2^32
