@@ -202,7 +202,7 @@ constexpr int kMpTile = kMpThreads * kMpIpt;
 #define TC_MP_MIN_BLOCKS 6
 #endif
 #ifndef TC_MP_SCATTER_MIN_BLOCKS
-#define TC_MP_SCATTER_MIN_BLOCKS 5
+#define TC_MP_SCATTER_MIN_BLOCKS 4
 #endif
 
 int64_t mp_tiles(int64_t n, int64_t nnz) { return (n + nnz + kMpTile - 1) / kMpTile; }
@@ -327,6 +327,15 @@ __global__ void k_popc(const unsigned* __restrict__ mask, int64_t nw, int32_t* _
 // read them as whole aligned 16-byte vectors; it also records each row's
 // smallest and largest rank id.
 // ============================================================================
+// Partition classes of an oriented edge (u, v) with a = d+(u), b = d+(v); see a-4 below.
+enum { kSkip = 0, kSmall = 1, kPivot = 2 };
+
+__device__ __forceinline__ int edge_class(int a, int b, int small_max) {
+    if (a <= 1 || b == 0) return kSkip;
+    if (max(a, b) <= small_max) return kSmall;
+    return kPivot;
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                              const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -385,11 +394,17 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                                                                const int32_t* __restrict__ rank, const int32_t* __restrict__ row_graph,
                                                                const int64_t* __restrict__ vtx_off, const unsigned* __restrict__ keep,
                                                                const int64_t* __restrict__ kpre, const int64_t* __restrict__ rpp,
+                                                               const int32_t* __restrict__ dp, int small_max,
                                                                int32_t* __restrict__ colp, int32_t* __restrict__ colr,
-                                                               int2* __restrict__ rspan) {
+                                                               int2* __restrict__ rspan, unsigned* __restrict__ umask,
+                                                               unsigned* __restrict__ vmask, int32_t* __restrict__ nv,
+                                                               DevCounters* __restrict__ dc) {
     __shared__ MpTile<BATCH> S;
     __shared__ int s_mn[kMpTile + 1], s_mx[kMpTile + 1];
+    __shared__ unsigned long long s_piv, s_small;
     const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) { s_piv = 0; s_small = 0; }
+    unsigned long long my_piv = 0, my_small = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         for (int k = threadIdx.x; k <= kMpTile; k += blockDim.x) {
             s_mn[k] = 0x7fffffff;
@@ -400,7 +415,11 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
         const int ne = S.ne, nr = S.nr;
         // colr position of a kept entry = its colp position + the padding of
         // the rows before its row (du is not needed here and is reused)
-        for (int k = threadIdx.x; k < nr; k += blockDim.x) S.du[k] = (int)(colr_row(rpp, i0 + k) - rpp[i0 + k]);
+        // (cs, used only to find each entry's row, now holds d+ of the row)
+        for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+            S.du[k] = (int)(colr_row(rpp, i0 + k) - rpp[i0 + k]);
+            S.cs[k] = dp[i0 + k];
+        }
         __syncthreads();
         // all loads of the tile first: keep words and lists, then the rank gathers
         unsigned kw[kMpIpt];
@@ -417,21 +436,50 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                 vv[q] = col[g] + (BATCH ? S.base[S.row[e]] : 0);
             }
         }
+        int bb[kMpIpt];
 #pragma unroll
-        for (int q = 0; q < kMpIpt; ++q) rr[q] = kw[q] ? rank[vv[q]] : 0;
+        for (int q = 0; q < kMpIpt; ++q) {
+            rr[q] = kw[q] ? rank[vv[q]] : 0;
+            bb[q] = kw[q] ? dp[vv[q]] : 0;
+        }
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
             const bool valid = e < ne;
             int k = 0xffff, mn = 0x7fffffff, mx = -1;
+            int64_t pos = 0;
+            bool pu = false, pv = false;
             if (valid) {
                 k = S.row[e];
                 if (kw[q]) {
                     const int64_t g = j0 + e;
-                    const int64_t pos = bits_before(keep, kpre, g);
+                    pos = bits_before(keep, kpre, g);
                     colp[pos] = vv[q];
                     colr[pos + S.du[k]] = rr[q];
                     mn = mx = rr[q];
+                    // a-4 classification of the oriented edge (u, v) at position pos
+                    const int a = S.cs[k], b = bb[q];
+                    const int cls = edge_class(a, b, small_max);
+                    pu = cls == kPivot && a >= b;
+                    pv = cls == kPivot && a < b;
+                    my_small += cls == kSmall;
+                    my_piv += pu || pv;
+                    if (pv) atomicAdd(&nv[vv[q]], 1);
+                }
+            }
+            // the warp's kept entries sit at consecutive positions: one bit
+            // pattern per mask, placed at the first kept entry's position
+            const unsigned kb = __ballot_sync(0xffffffffu, kw[q] != 0 && valid);
+            if (kb) {
+                const unsigned lt = (1u << lane) - 1u;
+                const int idx = __popc(kb & lt);
+                const unsigned ub = __reduce_or_sync(0xffffffffu, pu ? (1u << idx) : 0u);
+                const unsigned vb2 = __reduce_or_sync(0xffffffffu, pv ? (1u << idx) : 0u);
+                const int first = __ffs(kb) - 1;
+                const int64_t p0 = __shfl_sync(0xffffffffu, pos, first);
+                if (lane == first) {
+                    or_bits(umask, p0, ub);
+                    or_bits(vmask, p0, vb2);
                 }
             }
             // segmented min / max over runs of equal rows within the warp
@@ -462,6 +510,16 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
             }
         }
         __syncthreads();
+    }
+    for (int o = 16; o; o >>= 1) {
+        my_piv += __shfl_xor_sync(0xffffffffu, my_piv, o);
+        my_small += __shfl_xor_sync(0xffffffffu, my_small, o);
+    }
+    if (lane == 0) { atomicAdd(&s_piv, my_piv); atomicAdd(&s_small, my_small); }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&dc->n_pivot_edges, s_piv);
+        atomicAdd(&dc->n_small_edges, s_small);
     }
 }
 
@@ -547,66 +605,9 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const 
 //   nV(p)   = size of p's V-part, Vpre(p) = sum of nV(q) over q < p,
 // prp[p] = U(rpp[p]) + Vpre(p), a U-part entry x of row u lands at
 // U(x) + Vpre(u), and the V-part of p fills the slots just below prp[p+1].
+// The classification itself (the U and V bit masks over the oriented entries
+// and nV) is done by k_orient_scatter as it places each kept entry.
 // ============================================================================
-enum { kSkip = 0, kSmall = 1, kPivot = 2 };
-
-__device__ __forceinline__ int edge_class(int a, int b, int small_max) {
-    if (a <= 1 || b == 0) return kSkip;
-    if (max(a, b) <= small_max) return kSmall;
-    return kPivot;
-}
-
-__global__ void __launch_bounds__(kMpThreads) k_pivot_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
-                                                            const int64_t* __restrict__ rpp, const int32_t* __restrict__ colp,
-                                                            const int32_t* __restrict__ dp, int small_max,
-                                                            unsigned* __restrict__ umask, unsigned* __restrict__ vmask,
-                                                            int32_t* __restrict__ nv, DevCounters* __restrict__ dc) {
-    __shared__ MpTile<false> S;
-    __shared__ unsigned long long s_piv, s_small;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) { s_piv = 0; s_small = 0; }
-    unsigned long long my_piv = 0, my_small = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        mp_tile<false>(S, t, n, coord, rpp, nullptr, nullptr);
-        const int64_t j0 = S.j0;
-        const int ne = S.ne;
-        int av[kMpIpt], vv[kMpIpt], bv[kMpIpt];
-#pragma unroll
-        for (int q = 0; q < kMpIpt; ++q) {
-            const int e = q * kMpThreads + threadIdx.x;
-            av[q] = e < ne ? S.du[S.row[e]] : 0;
-            vv[q] = av[q] > 1 ? colp[j0 + e] : 0;
-        }
-#pragma unroll
-        for (int q = 0; q < kMpIpt; ++q) bv[q] = av[q] > 1 ? dp[vv[q]] : 0;
-#pragma unroll
-        for (int q = 0; q < kMpIpt; ++q) {
-            const int cls = edge_class(av[q], bv[q], small_max);
-            const bool pu = cls == kPivot && av[q] >= bv[q];
-            const bool pv = cls == kPivot && av[q] < bv[q];
-            my_small += cls == kSmall;
-            if (pv) atomicAdd(&nv[vv[q]], 1);
-            my_piv += pu + pv;
-            const unsigned bu = __ballot_sync(0xffffffffu, pu), bw = __ballot_sync(0xffffffffu, pv);
-            if (lane == 0) {
-                const int64_t g = j0 + q * kMpThreads + w * 32;
-                or_bits(umask, g, bu);
-                or_bits(vmask, g, bw);
-            }
-        }
-        __syncthreads();
-    }
-    for (int o = 16; o; o >>= 1) {
-        my_piv += __shfl_xor_sync(0xffffffffu, my_piv, o);
-        my_small += __shfl_xor_sync(0xffffffffu, my_small, o);
-    }
-    if (lane == 0) { atomicAdd(&s_piv, my_piv); atomicAdd(&s_small, my_small); }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&dc->n_pivot_edges, s_piv);
-        atomicAdd(&dc->n_small_edges, s_small);
-    }
-}
 
 // prp[p] = U(rpp[p]) + Vpre(p), p = 0 .. n
 __global__ void k_pivot_offsets(int64_t n, const int64_t* __restrict__ rpp, const unsigned* __restrict__ umask,
@@ -878,9 +879,19 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         PhaseScope ph(ctx, kPhOrientScatter, s);
         // padding (and the gaps between rows) of colr read as -1
         cudaMemsetAsync(o->colr, 0xff, sizeof(int32_t) * (std::max<int64_t>(m, 1) + 3 * n + 4), s);
+        // the scatter also classifies each oriented edge for the partition (a-4)
+        cudaMemsetAsync(pc, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), s);
+        cudaMemsetAsync(umask, 0, sizeof(unsigned) * uw, s);
+        cudaMemsetAsync(vmask, 0, sizeof(unsigned) * uw, s);
         if (nt1 > 0) {
-            if (batch) k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
-            else k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre, o->rpp, o->colp, o->colr, o->rspan);
+            if (batch)
+                k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre,
+                                                                 o->rpp, o->dplus, tun.small_max, o->colp, o->colr, o->rspan,
+                                                                 umask, vmask, pc, o->dc);
+            else
+                k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre,
+                                                                  o->rpp, o->dplus, tun.small_max, o->colp, o->colr, o->rspan,
+                                                                  umask, vmask, pc, o->dc);
             TC_LAUNCH(ctx);
         }
     }
@@ -896,12 +907,8 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     // a-4: classify, group oriented edges by pivot
     {
         PhaseScope ph(ctx, kPhPivotCount, s);
-        cudaMemsetAsync(pc, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), s);
-        cudaMemsetAsync(umask, 0, sizeof(unsigned) * uw, s);
-        cudaMemsetAsync(vmask, 0, sizeof(unsigned) * uw, s);
         k_mp_coords<<<grid_for(nt2 + 1, 256, ns), 256, 0, s>>>(n, m, o->rpp, nt2, coord);
-        if (nt2 > 0) k_pivot_flags<<<g2, kMpThreads, 0, s>>>(n, nt2, coord, o->rpp, o->colp, o->dplus, tun.small_max, umask, vmask, pc, o->dc);
-        ctx->launches += 2;
+        TC_LAUNCH(ctx);
     }
     {
         PhaseScope ph(ctx, kPhPivotScan, s);
