@@ -119,9 +119,15 @@ cudaError_t scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* tm
 // ============================================================================
 // a-1  degree: d(v) = row_ptr[v+1] - row_ptr[v]
 // ============================================================================
-__global__ void k_degree(int64_t n, const int64_t* __restrict__ rp, int32_t* __restrict__ deg) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        deg[v] = (int32_t)(rp[v + 1] - rp[v]);
+__global__ void k_degree(int64_t n, const int64_t* __restrict__ rp, int32_t* __restrict__ deg, int* __restrict__ max_deg) {
+    int mx = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int32_t)(rp[v + 1] - rp[v]);
+        deg[v] = d;
+        mx = max(mx, d);
+    }
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(max_deg, mx);
 }
 
 // batch: row_graph[v] = graph of global vertex v
@@ -193,6 +199,11 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ r
 // t * kMpTile, found by binary search (a row end is taken before an entry
 // with the same offset).
 // ============================================================================
+// CTA work items carry this many times `chunk` partners (one table build and
+// flush serve them all; at most 32767 keeps the 16-bit direct cells exact)
+#ifndef TC_CTA_CHUNK_MUL
+#define TC_CTA_CHUNK_MUL 2
+#endif
 constexpr int kMpThreads = 256;
 constexpr int kMpIpt = 8;
 constexpr int kMpTile = kMpThreads * kMpIpt;
@@ -378,14 +389,22 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(i
     }
 }
 
-// rpp[u] = kept entries before row u, and d+(u)
+// rpp[u] = kept entries before row u, and d+(u) (and its maximum)
 __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned* __restrict__ keep,
-                       const int64_t* __restrict__ kpre, int64_t* __restrict__ rpp, int32_t* __restrict__ dplus) {
+                       const int64_t* __restrict__ kpre, int64_t* __restrict__ rpp, int32_t* __restrict__ dplus,
+                       int* __restrict__ max_dplus) {
+    int mx = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = bits_before(keep, kpre, rp[u]);
         rpp[u] = s;
-        if (u < n) dplus[u] = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
+        if (u < n) {
+            const int d = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
+            dplus[u] = d;
+            mx = max(mx, d);
+        }
     }
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(max_dplus, mx);
 }
 
 template <bool BATCH>
@@ -535,7 +554,9 @@ constexpr int kSortWarps = TC_SORT_WARPS;
 
 __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const int64_t* __restrict__ rpp,
                                                                const int32_t* __restrict__ dplus,
+                                                               const int* __restrict__ max_dplus,
                                                                int32_t* __restrict__ colr) {
+    if (*max_dplus < kSortedMin) return;  // no row to partition
     extern __shared__ int sbuf[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int* buf = sbuf + w * (kSortedMax + kRankLevels);
@@ -657,10 +678,10 @@ __global__ void __launch_bounds__(kMpThreads, 1) k_pivot_scatter(int64_t n, int6
 }
 
 // Work items per pivot.  Warp class (d+(p) <= warp_max): one item per chunk of
-// partners.  CTA class: one item per (segment of the pivot list, chunk of
+// partners.  CTA class: one item per (segment of the pivot list, chunk_c
 // partners); a segment holds at most table_cap keys.
 __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restrict__ dp, const int64_t* __restrict__ prp,
-                                               int warp_max, int table_cap, int chunk,
+                                               int warp_max, int table_cap, int chunk, int chunk_c,
                                                Item* __restrict__ iw, int64_t iw_cap,
                                                Item* __restrict__ ic, int64_t ic_cap,
                                                DevCounters* __restrict__ dc) {
@@ -670,8 +691,9 @@ __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restr
         const int64_t p = t0 + threadIdx.x;
         int pcnt = 0, d = 0;
         if (p < n) { pcnt = (int)(prp[p + 1] - prp[p]); d = dp[p]; }
-        const int nch = (pcnt + chunk - 1) / chunk;
         const bool is_warp = d <= warp_max;
+        const int ck = is_warp ? chunk : chunk_c;
+        const int nch = (pcnt + ck - 1) / ck;
         const int nseg = is_warp ? 1 : (d + table_cap - 1) / table_cap;
         const long long cw = (pcnt > 0 && is_warp) ? nch : 0;
         const long long cc = (pcnt > 0 && !is_warp) ? (long long)nch * nseg : 0;
@@ -691,7 +713,7 @@ __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restr
             long long k = 0;
             for (int sg = 0; sg < nseg; ++sg)
                 for (int c = 0; c < nch; ++c, ++k)
-                    if (bc + k < ic_cap) ic[bc + k] = Item{(int)p, sg, c * chunk, min(pcnt, (c + 1) * chunk)};
+                    if (bc + k < ic_cap) ic[bc + k] = Item{(int)p, sg, c * chunk_c, (int)min((int64_t)pcnt, (int64_t)(c + 1) * chunk_c)};
         }
         __syncthreads();
     }
@@ -777,7 +799,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
             TC_LAUNCH(ctx);
         }
         if (n > 0) {
-            k_degree<<<grid_for(n, 256, ns), 256, 0, s>>>(n, row_ptr, deg);
+            k_degree<<<grid_for(n, 256, ns), 256, 0, s>>>(n, row_ptr, deg, &o->dc->max_deg);
             TC_LAUNCH(ctx);
         }
     }
@@ -809,7 +831,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
             k_rank_keys<<<grid_for(n, 256, ns), 256, 0, s>>>(n, deg, b, ka);
             // the keys are written in id order and the sort is stable, so
             // sorting the degree bits alone yields (degree, id) order
-            radix_sort_u64(ka, kb, n, 2 * b, s, &sorted, &ctx->launches, b);
+            radix_sort_u64(ka, kb, n, 2 * b, s, &sorted, &ctx->launches, b, &o->dc->max_deg, b);
             k_rank_from_sorted<<<grid_for(n, 256, ns), 256, 0, s>>>(n, sorted, b, o->rank, o->perm);
             ctx->launches += 2;
         }
@@ -872,7 +894,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         k_popc<<<grid_for(kw, 256, ns), 256, 0, s>>>(keep, kw, wpc);
         scan_i32_to_i64(wpc, kpre, kw, wtmp, wtb, s);
         // row offsets and d+
-        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rpp, o->dplus);
+        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rpp, o->dplus, &o->dc->max_dplus);
         ctx->launches += 5;
     }
     {
@@ -901,7 +923,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         const size_t sm = sizeof(int) * (kSortedMax + kRankLevels) * kSortWarps;
         cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         const unsigned sg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kSortWarps - 1) / (32 * kSortWarps), (int64_t)ns * 32 / kSortWarps));
-        k_sort_rows<<<sg, 32 * kSortWarps, sm, s>>>(n, o->rpp, o->dplus, o->colr);
+        k_sort_rows<<<sg, 32 * kSortWarps, sm, s>>>(n, o->rpp, o->dplus, &o->dc->max_dplus, o->colr);
         TC_LAUNCH(ctx);
     }
     // a-4: classify, group oriented edges by pivot
@@ -930,6 +952,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     if (n > 0) {
         PhaseScope ph(ctx, kPhItems, s);
         k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->dplus, o->prp, tun.warp_max, tun.table_cap, tun.chunk,
+                                                     (int)std::min<int64_t>((int64_t)tun.chunk * TC_CTA_CHUNK_MUL, 32767),
                                                      o->items_warp, o->items_warp_cap, o->items_cta, o->items_cta_cap, o->dc);
         TC_LAUNCH(ctx);
     }

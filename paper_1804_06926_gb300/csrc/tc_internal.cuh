@@ -21,6 +21,7 @@ struct DevCounters {
     unsigned long long n_small_edges;  // oriented edges merged thread-per-edge
     int error;                         // validation verdict (0 = ok)
     int max_dplus;                     // max out-degree after orientation
+    int max_deg;                       // max degree of the input
 };
 
 // One unit of pivot work: intersect the pivot's list segment
@@ -148,9 +149,12 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
                                 const int32_t* col, const int64_t* vtx_off, int64_t G,
                                 bool validate, tc_ocsr** out, cudaStream_t s);
 
-// Stable LSD radix sort of uint64 keys on bits [low_bit, key_bits).
+// Stable LSD radix sort of uint64 keys on bits [low_bit, key_bits).  With
+// maxv (device), bits [vbase, ...) of every key are at most *maxv, and the
+// passes over digits that are then zero for all keys reduce to copies.
 cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64_t K, int key_bits, cudaStream_t s,
-                           unsigned long long** sorted, long long* launches, int low_bit);
+                           unsigned long long** sorted, long long* launches, int low_bit,
+                           const int* maxv = nullptr, int vbase = 0);
 
 // Canonicalise a device edge list into a device CSR (library-owned buffers).
 tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t npairs, const int32_t* src, const int32_t* dst,

@@ -38,8 +38,17 @@ __global__ void k_make_keys(int64_t np, const int32_t* __restrict__ src, const i
     }
 }
 
+// A pass is trivial when every key's digit is 0: with maxv given, digit
+// bits [shift, shift+8) of a key are bits [shift-vbase, ...) of a value that
+// is at most *maxv.  A trivial pass is the identity and is done as a copy.
+__device__ __forceinline__ bool rs_trivial(const int* maxv, int vbase, int shift) {
+    return maxv && shift >= vbase && ((unsigned)*maxv >> (shift - vbase)) == 0u;
+}
+
 __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long* __restrict__ keys, int64_t K, int shift,
-                                                        int32_t* __restrict__ hist, int64_t ntiles) {
+                                                        int32_t* __restrict__ hist, int64_t ntiles,
+                                                        const int* __restrict__ maxv, int vbase) {
+    if (rs_trivial(maxv, vbase, shift)) return;
     __shared__ int h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -56,11 +65,20 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long
 // Stable scatter: keys of a tile keep their order within each digit.
 __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long long* __restrict__ in,
                                                            unsigned long long* __restrict__ out, int64_t K, int shift,
-                                                           const int64_t* __restrict__ off, int64_t ntiles) {
+                                                           const int64_t* __restrict__ off, int64_t ntiles,
+                                                           const int* __restrict__ maxv, int vbase) {
     __shared__ int wcnt[kRsWarps][256];
     __shared__ int run[256];
     __shared__ long long base[256];
     const int tid = threadIdx.x, warp = tid >> 5;
+    if (rs_trivial(maxv, vbase, shift)) {
+        const int64_t t0 = (int64_t)blockIdx.x * kRsTile;
+        for (int r = 0; r < kRsItems; ++r) {
+            const int64_t i = t0 + r * kRsThreads + tid;
+            if (i < K) out[i] = in[i];
+        }
+        return;
+    }
     run[tid] = 0;
     base[tid] = off[(int64_t)tid * ntiles + blockIdx.x];
     __syncthreads();
@@ -95,9 +113,10 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long l
 
 // LSD radix sort of K keys on bits [low_bit, key_bits) (8 bits per pass,
 // stable).  ka holds the input, kb is scratch of the same size; *sorted
-// receives whichever of the two holds the result.
+// receives whichever of the two holds the result (a pass made trivial by
+// maxv still copies, so the ping-pong order never depends on device data).
 cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64_t K, int key_bits, cudaStream_t s,
-                           unsigned long long** sorted, long long* launches, int low_bit) {
+                           unsigned long long** sorted, long long* launches, int low_bit, const int* maxv, int vbase) {
     *sorted = ka;
     if (K <= 0) return cudaSuccess;
     const int64_t ntiles = (K + kRsTile - 1) / kRsTile;
@@ -111,9 +130,9 @@ cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64
     if (e == cudaSuccess) e = dev_alloc(&stmp, stb, s);
     if (e == cudaSuccess) {
         for (int shift = low_bit; shift < key_bits; shift += 8) {
-            k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, K, shift, hist, ntiles);
+            k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, K, shift, hist, ntiles, maxv, vbase);
             scan_i32_to_i64(hist, hoff, nh, stmp, stb, s);
-            k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, kb, K, shift, hoff, ntiles);
+            k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, kb, K, shift, hoff, ntiles, maxv, vbase);
             std::swap(ka, kb);
             if (launches) *launches += 5;
         }
