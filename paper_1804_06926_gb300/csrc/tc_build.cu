@@ -335,8 +335,7 @@ __global__ void k_popc(const unsigned* __restrict__ mask, int64_t nw, int32_t* _
 // row_ptr[u] (k_rows).  Pass 2 scatters the kept neighbours: vertex ids to
 // colp, rank ids to colr, whose rows start at multiples of 4 (colr_row) and
 // are padded with -1 (colr is cleared to -1 first) so that the count kernels
-// read them as whole aligned 16-byte vectors; it also records each row's
-// smallest and largest rank id.
+// read them as whole aligned 16-byte vectors.
 // ============================================================================
 // Partition classes of an oriented edge (u, v) with a = d+(u), b = d+(v); see a-4 below.
 enum { kSkip = 0, kSmall = 1, kPivot = 2 };
@@ -351,18 +350,13 @@ template <bool BATCH>
 __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                              const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                              const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
-                                                             const int64_t* __restrict__ vtx_off, unsigned* __restrict__ keep,
-                                                             int2* __restrict__ rspan) {
+                                                             const int64_t* __restrict__ vtx_off, unsigned* __restrict__ keep) {
     __shared__ MpTile<BATCH> S;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         mp_tile<BATCH>(S, t, n, coord, rp, row_graph, vtx_off);
         const int64_t i0 = S.i0, j0 = S.j0;
         const int ne = S.ne, nr = S.nr;
-        // rows that continue into another tile collect their rank span with
-        // atomics in pass 2; start them empty here
-        if (threadIdx.x == 0 && nr > 0 && (!S.first_full || S.nend == 0)) rspan[i0] = make_int2(0x7fffffff, -1);
-        if (threadIdx.x == 1 && nr > 0 && nr - 1 >= S.nend) rspan[i0 + nr - 1] = make_int2(0x7fffffff, -1);
         // all loads of the tile first (8 independent streams, then 8 gathers)
         int32_t vv[kMpIpt];
         int dv[kMpIpt];
@@ -415,20 +409,15 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                                                                const int64_t* __restrict__ kpre, const int64_t* __restrict__ rpp,
                                                                const int32_t* __restrict__ dp, int small_max,
                                                                int32_t* __restrict__ colp, int32_t* __restrict__ colr,
-                                                               int2* __restrict__ rspan, unsigned* __restrict__ umask,
+                                                               unsigned* __restrict__ umask,
                                                                unsigned* __restrict__ vmask, int32_t* __restrict__ nv,
                                                                DevCounters* __restrict__ dc) {
     __shared__ MpTile<BATCH> S;
-    __shared__ int s_mn[kMpTile + 1], s_mx[kMpTile + 1];
     __shared__ unsigned long long s_piv, s_small;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) { s_piv = 0; s_small = 0; }
     unsigned long long my_piv = 0, my_small = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        for (int k = threadIdx.x; k <= kMpTile; k += blockDim.x) {
-            s_mn[k] = 0x7fffffff;
-            s_mx[k] = -1;
-        }
         mp_tile<BATCH>(S, t, n, coord, rp, row_graph, vtx_off);
         const int64_t i0 = S.i0, j0 = S.j0;
         const int ne = S.ne, nr = S.nr;
@@ -465,17 +454,15 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
             const bool valid = e < ne;
-            int k = 0xffff, mn = 0x7fffffff, mx = -1;
             int64_t pos = 0;
             bool pu = false, pv = false;
             if (valid) {
-                k = S.row[e];
+                const int k = S.row[e];
                 if (kw[q]) {
                     const int64_t g = j0 + e;
                     pos = bits_before(keep, kpre, g);
                     colp[pos] = vv[q];
                     colr[pos + S.du[k]] = rr[q];
-                    mn = mx = rr[q];
                     // a-4 classification of the oriented edge (u, v) at position pos
                     const int a = S.cs[k], b = bb[q];
                     const int cls = edge_class(a, b, small_max);
@@ -501,32 +488,6 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                     or_bits(vmask, p0, vb2);
                 }
             }
-            // segmented min / max over runs of equal rows within the warp
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int k2 = __shfl_down_sync(0xffffffffu, k, o);
-                const int mn2 = __shfl_down_sync(0xffffffffu, mn, o);
-                const int mx2 = __shfl_down_sync(0xffffffffu, mx, o);
-                if (lane + o < 32 && k2 == k) {
-                    mn = min(mn, mn2);
-                    mx = max(mx, mx2);
-                }
-            }
-            const int kprev = __shfl_up_sync(0xffffffffu, k, 1);
-            if (valid && (lane == 0 || kprev != k) && mx >= 0) {
-                atomicMin(&s_mn[k], mn);
-                atomicMax(&s_mx[k], mx);
-            }
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < nr; k += blockDim.x) {
-            const int64_t u = i0 + k;
-            if (k < S.nend && (k > 0 || S.first_full)) {
-                rspan[u] = make_int2(s_mn[k], s_mx[k]);
-            } else if (s_mx[k] >= 0) {
-                atomicMin(&rspan[u].x, s_mn[k]);
-                atomicMax(&rspan[u].y, s_mx[k]);
-            }
         }
         __syncthreads();
     }
@@ -543,10 +504,14 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
 }
 
 
-// Partition the colr rows with kSortedMin <= d+ <= kSortedMax into buckets of
-// descending rank_level(n - x) (see tc_internal.cuh): one warp per row, the
-// row staged in the warp's shared-memory buffer, a histogram of levels, their
-// exclusive prefix in descending order, and an atomic scatter back.
+// Two jobs on the colr rows, one warp per row:
+//  * rspan[u] = (smallest, largest) rank id of every row with d+ > warp_max,
+//    the rows a CTA table may be built from (the CTA kernel reads it to pick
+//    the table kind of a whole-row item);
+//  * rows with kSortedMin <= d+ <= kSortedMax are partitioned into buckets of
+//    descending rank_level(n - x) (see tc_internal.cuh): the row is staged in
+//    the warp's shared-memory buffer, levels are counted, their exclusive
+//    prefix taken in descending order, and the row scattered back.
 #ifndef TC_SORT_WARPS
 #define TC_SORT_WARPS 4
 #endif
@@ -554,9 +519,10 @@ constexpr int kSortWarps = TC_SORT_WARPS;
 
 __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const int64_t* __restrict__ rpp,
                                                                const int32_t* __restrict__ dplus,
-                                                               const int* __restrict__ max_dplus,
-                                                               int32_t* __restrict__ colr) {
-    if (*max_dplus < kSortedMin) return;  // no row to partition
+                                                               const int* __restrict__ max_dplus, int warp_max,
+                                                               int32_t* __restrict__ colr, int2* __restrict__ rspan) {
+    const int mdp = *max_dplus;
+    if (mdp < kSortedMin && mdp <= warp_max) return;  // no row to partition or span
     extern __shared__ int sbuf[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int* buf = sbuf + w * (kSortedMax + kRankLevels);
@@ -565,20 +531,35 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const 
     for (int64_t u0 = ((int64_t)blockIdx.x * kSortWarps + w) * 32; u0 < n; u0 += nwarps * 32) {
         const int64_t ul = u0 + lane;
         const int dl = ul < n ? dplus[ul] : 0;
-        unsigned todo = __ballot_sync(0xffffffffu, dl >= kSortedMin && dl <= kSortedMax);
+        unsigned todo = __ballot_sync(0xffffffffu, (dl >= kSortedMin && dl <= kSortedMax) || dl > warp_max);
         while (todo) {
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             const int64_t u = u0 + src;
             const int d = __shfl_sync(0xffffffffu, dl, src);
+            const bool part = d >= kSortedMin && d <= kSortedMax;
             int32_t* row = colr + colr_row(rpp, u);
-            for (int i = lane; i < kRankLevels; i += 32) cur[i] = 0;
-            __syncwarp();
+            int mn = 0x7fffffff, mx = -1;
+            if (part) {
+                for (int i = lane; i < kRankLevels; i += 32) cur[i] = 0;
+                __syncwarp();
+            }
             for (int i = lane; i < d; i += 32) {
                 const int x = row[i];
-                buf[i] = x;
-                atomicAdd(&cur[rank_level((unsigned)(n - x))], 1);
+                mn = min(mn, x);
+                mx = max(mx, x);
+                if (part) {
+                    buf[i] = x;
+                    atomicAdd(&cur[rank_level((unsigned)(n - x))], 1);
+                }
             }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if (lane == 0) rspan[u] = make_int2(mn, mx);
+            if (!part) continue;
             __syncwarp();
             // exclusive prefix over levels kRankLevels-1 .. 0 (lane l: 8 levels)
             int c[8], t = 0;
@@ -883,8 +864,8 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         cudaMemsetAsync(keep, 0, sizeof(unsigned) * kw, s);
         k_mp_coords<<<grid_for(nt1 + 1, 256, ns), 256, 0, s>>>(n, nnz, row_ptr, nt1, coord);
         if (nt1 > 0) {
-            if (batch) k_orient_flags<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, o->row_graph, vtx_off, keep, o->rspan);
-            else k_orient_flags<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, nullptr, nullptr, keep, o->rspan);
+            if (batch) k_orient_flags<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, o->row_graph, vtx_off, keep);
+            else k_orient_flags<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, nullptr, nullptr, keep);
         }
         ctx->launches += 2;
     }
@@ -908,22 +889,23 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         if (nt1 > 0) {
             if (batch)
                 k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre,
-                                                                 o->rpp, o->dplus, tun.small_max, o->colp, o->colr, o->rspan,
+                                                                 o->rpp, o->dplus, tun.small_max, o->colp, o->colr,
                                                                  umask, vmask, pc, o->dc);
             else
                 k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre,
-                                                                  o->rpp, o->dplus, tun.small_max, o->colp, o->colr, o->rspan,
+                                                                  o->rpp, o->dplus, tun.small_max, o->colp, o->colr,
                                                                   umask, vmask, pc, o->dc);
             TC_LAUNCH(ctx);
         }
     }
-    // colr rows of the partners whose lists the count kernels stream, sorted by rank
+    // rank spans of the rows CTA tables are built from; level partition of the
+    // rows whose lists the CTA kernel streams
     if (n > 0) {
         PhaseScope ph(ctx, kPhRowSort, s);
         const size_t sm = sizeof(int) * (kSortedMax + kRankLevels) * kSortWarps;
         cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         const unsigned sg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kSortWarps - 1) / (32 * kSortWarps), (int64_t)ns * 32 / kSortWarps));
-        k_sort_rows<<<sg, 32 * kSortWarps, sm, s>>>(n, o->rpp, o->dplus, &o->dc->max_dplus, o->colr);
+        k_sort_rows<<<sg, 32 * kSortWarps, sm, s>>>(n, o->rpp, o->dplus, &o->dc->max_dplus, tun.warp_max, o->colr, o->rspan);
         TC_LAUNCH(ctx);
     }
     // a-4: classify, group oriented edges by pivot
