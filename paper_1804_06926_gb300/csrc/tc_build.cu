@@ -642,17 +642,34 @@ __global__ void __launch_bounds__(kMpThreads, 1) k_pivot_scatter(int64_t n, int6
                 vw[q] = vmask[g >> 5];
             }
         }
+        // every load and atomic of the tile first, then the stores: the V-part
+        // slots come from returned atomics, whose latency the batch hides
+        int32_t vv[kMpIpt];
+        int cu[kMpIpt];      // U-part: set bits of the entry's mask word below it; -1 otherwise
+        unsigned pvm = 0;    // V-part entries (bit q)
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int64_t g = j0 + q * kMpThreads + threadIdx.x;
+            const unsigned bit = (unsigned)(g & 31);
+            const bool pu = (uw[q] >> bit) & 1u, pv = (vw[q] >> bit) & 1u;  // 0 past the tile
+            cu[q] = pu ? __popc(uw[q] & ((1u << bit) - 1u)) : -1;
+            if (pv) pvm |= 1u << q;
+            vv[q] = (pu || pv) ? colp[g] : 0;
+        }
+        int64_t dst[kMpIpt];
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
             const int64_t g = j0 + e;
-            const int bit = (int)(g & 31);
-            const bool pu = (uw[q] >> bit) & 1u, pv = (vw[q] >> bit) & 1u;
-            if (!pu && !pv) continue;
-            const int64_t u = i0 + S.row[e];
-            const int32_t v = colp[g];
-            if (pu) pcol[upre[g >> 5] + __popc(uw[q] & ((1u << bit) - 1u)) + vpre[u]] = v;
-            else pcol[prp[(int64_t)v + 1] - atomicSub(&nv[v], 1)] = (int32_t)u;
+            dst[q] = -1;
+            if (cu[q] >= 0) dst[q] = upre[g >> 5] + cu[q] + vpre[i0 + S.row[e]];
+            else if ((pvm >> q) & 1u) dst[q] = prp[(int64_t)vv[q] + 1] - atomicSub(&nv[vv[q]], 1);
+        }
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            if (dst[q] < 0) continue;
+            const int e = q * kMpThreads + threadIdx.x;
+            pcol[dst[q]] = cu[q] >= 0 ? vv[q] : (int32_t)(i0 + S.row[e]);
         }
         __syncthreads();
     }
