@@ -213,6 +213,7 @@ struct Table {
     unsigned* cell32;      // direct mode, 32-bit cells
     int lo, span;
     int lev;               // rank_level(n - smallest key): where walks of partitioned lists may stop
+    unsigned sbase;        // shared-memory address of the cell array (direct modes)
 };
 
 // Probe x; on a hit count it (per-vertex counter of x when PV) and return
@@ -454,15 +455,16 @@ __device__ __forceinline__ void red_shared_if(bool p, const void* addr, unsigned
         : "memory");
 }
 
-// Shared-memory atomic add under a predicate, returning the old value (0 when
-// the predicate is false).
-__device__ __forceinline__ unsigned atom_shared_add_if(bool p, const void* addr, unsigned v) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
+// The probe of a direct cell with per-vertex counts, as one predicated
+// shared atomic: if off < span, add v to the 32-bit word at shared address
+// addr and return its old value, else return 0.  The span test is the
+// predicate itself, so a probe costs the offset, the address and the atomic.
+__device__ __forceinline__ unsigned atom_probe(unsigned off, unsigned span, unsigned addr, unsigned v) {
     unsigned r;
     asm volatile(
-        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\tmov.u32 %0, 0;\n\t@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
+        "{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %1, %2;\n\tmov.u32 %0, 0;\n\t@q atom.shared.add.u32 %0, [%3], %4;\n\t}"
         : "=r"(r)
-        : "r"(a), "r"(v), "r"((unsigned)p)
+        : "r"(off), "r"(span), "r"(addr), "r"(v)
         : "memory");
     return r;
 }
@@ -473,18 +475,16 @@ template <int MODE, bool PV>
 __device__ __forceinline__ int probe1(const Table& t, int x) {
     if (MODE == kModeDirect32) {
         const unsigned off = (unsigned)(x - t.lo);
-        const bool in = off < (unsigned)t.span;
-        if (PV) return (int)(atom_shared_add_if(in, t.cell32 + off, 1u) >> 31);
-        const unsigned c = in ? t.cell32[off] : 0u;
+        if (PV) return (int)(atom_probe(off, (unsigned)t.span, t.sbase + (off << 2), 1u) >> 31);
+        const unsigned c = off < (unsigned)t.span ? t.cell32[off] : 0u;
         return c != 0u ? 1 : 0;
     } else if (MODE == kModeDirect) {
         const unsigned off = (unsigned)(x - t.lo);
-        const bool in = off < (unsigned)t.span;
         if (PV) {
             const unsigned sh = (off & 1u) << 4;
-            return (int)((atom_shared_add_if(in, t.cell + (off & ~1u), 1u << sh) >> (15u + sh)) & 1u);
+            return (int)((atom_probe(off, (unsigned)t.span, t.sbase + ((off << 1) & ~3u), 1u << sh) >> (15u + sh)) & 1u);
         }
-        const unsigned c = in ? (unsigned)t.cell[off] : 0u;
+        const unsigned c = off < (unsigned)t.span ? (unsigned)t.cell[off] : 0u;
         return c != 0u ? 1 : 0;
     } else if (MODE == kModeBitmap) {
         const unsigned off = (unsigned)(x - t.lo);
@@ -722,6 +722,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
         Table tb{};
         tb.len = len;
         tb.lev = INT_MAX;
+        tb.sbase = (unsigned)__cvta_generic_to_shared(U);
         int mode = PROBE == kProbeHash ? kModeHash : kModeBsearch;
         if (PROBE == kProbeHash && a.bitmap_bits > 0) {
             int mn, mx;
