@@ -620,7 +620,10 @@ __global__ void k_pivot_offsets(int64_t n, const int64_t* __restrict__ rpp, cons
 }
 
 // nv[p] counts down from nV(p) while p's V-part is filled.
-__global__ void __launch_bounds__(kMpThreads, 1) k_pivot_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
+#ifndef TC_PSCATTER_MIN_BLOCKS
+#define TC_PSCATTER_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                               const int64_t* __restrict__ rpp, const int32_t* __restrict__ colp,
                                                               const unsigned* __restrict__ umask, const unsigned* __restrict__ vmask,
                                                               const int64_t* __restrict__ upre, const int64_t* __restrict__ vpre,

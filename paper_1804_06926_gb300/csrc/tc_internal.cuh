@@ -62,8 +62,11 @@ __host__ __device__ __forceinline__ int64_t colr_row(const int64_t* rpp, int64_t
 #ifndef TC_SORTED_MIN
 #define TC_SORTED_MIN 64
 #endif
+#ifndef TC_SORTED_MAX
+#define TC_SORTED_MAX 1024
+#endif
 constexpr int kSortedMin = TC_SORTED_MIN;
-constexpr int kSortedMax = 2048;
+constexpr int kSortedMax = TC_SORTED_MAX;
 constexpr int kRankLevels = 256;  // 32 octaves x 8
 __device__ __forceinline__ int rank_level(unsigned y) {  // 1 <= y < 2^32
     const int e = 31 - __clz(y);
