@@ -421,12 +421,14 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
         mp_tile<BATCH>(S, t, n, coord, rp, row_graph, vtx_off);
         const int64_t i0 = S.i0, j0 = S.j0;
         const int ne = S.ne, nr = S.nr;
-        // colr position of a kept entry = its colp position + the padding of
-        // the rows before its row (du is not needed here and is reused)
-        // (cs, used only to find each entry's row, now holds d+ of the row)
+        // colr position of a kept entry = its colp position + colr_row(u) - rpp[u]
+        // = pos + 3u + 3 - r, r = (rpp[u] + 3u + 3) mod 4 (kept in du, which is
+        // not needed here; the offset itself exceeds 32 bits for large u).
+        // cs, used only to find each entry's row, now holds d+ of the row.
         for (int k = threadIdx.x; k < nr; k += blockDim.x) {
-            S.du[k] = (int)(colr_row(rpp, i0 + k) - rpp[i0 + k]);
-            S.cs[k] = dp[i0 + k];
+            const int64_t u = i0 + k;
+            S.du[k] = (int)((rpp[u] + 3 * u + 3) & 3);
+            S.cs[k] = dp[u];
         }
         __syncthreads();
         // all loads of the tile first: keep words and lists, then the rank gathers
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                     const int64_t g = j0 + e;
                     pos = bits_before(keep, kpre, g);
                     colp[pos] = vv[q];
-                    colr[pos + S.du[k]] = rr[q];
+                    colr[pos + 3 * (i0 + k) + 3 - S.du[k]] = rr[q];
                     // a-4 classification of the oriented edge (u, v) at position pos
                     const int a = S.cs[k], b = bb[q];
                     const int cls = edge_class(a, b, small_max);
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restr
         __syncthreads();
         const long long bw = (long long)s_bw + ow, bc = (long long)s_bc + oc;
         for (int c = 0; c < (int)cw; ++c) {
-            if (bw + c < iw_cap) iw[bw + c] = Item{(int)p, 0, c * chunk, min(pcnt, (c + 1) * chunk)};
+            if (bw + c < iw_cap) iw[bw + c] = Item{(int)p, 0, c * chunk, (int)min((int64_t)pcnt, (int64_t)(c + 1) * chunk)};
         }
         if (cc) {
             long long k = 0;
