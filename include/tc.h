@@ -296,8 +296,9 @@ typedef struct tc_server_config {
     int32_t batch_graphs;      /* up to this many small requests waiting at the head of the queue
                                   (host CSR, no TC_VALIDATE, not resident) are fused into one batched
                                   build + count on one slot; default 32; 1 = never fuse */
-    int64_t batch_nnz;         /* a request is small when its CSR has at most this many entries; a
-                                  fused batch holds at most 8x this many; default 2^20 */
+    int64_t batch_nnz;         /* a request is small when its CSR has at most this many entries and
+                                  vertices; a fused batch holds at most 8x this many entries;
+                                  default 2^20 */
     int32_t reserved[4];
 } tc_server_config;
 

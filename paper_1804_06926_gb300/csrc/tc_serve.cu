@@ -250,8 +250,9 @@ struct tc_server {
     }
 
     bool fusable(const Request* r) const {
-        return r->csr && !(r->flags & TC_VALIDATE) && r->nnz <= cfg.batch_nnz && r->h_rp[0] == 0 &&
-               r->h_rp[r->n] == r->nnz;
+        // small in edges and in vertices (a fused batch stays far below 2^31 vertices)
+        return r->csr && !(r->flags & TC_VALIDATE) && r->nnz <= cfg.batch_nnz && r->n <= cfg.batch_nnz &&
+               r->h_rp[0] == 0 && r->h_rp[r->n] == r->nnz;
     }
 
     void free_job(BatchJob& b, cudaStream_t s) {
@@ -409,14 +410,15 @@ struct tc_server {
                 // fuse the small requests waiting together at the head of the queue
                 if (!hit && cfg.batch_graphs > 1 && queue.size() >= 2 && fusable(r)) {
                     std::vector<Request*> B;
-                    int64_t need = 0, nnz = 0;
+                    int64_t need = 0, nnz = 0, nv = 0;
                     for (Request* q : queue) {
                         if ((int)B.size() >= cfg.batch_graphs || !fusable(q) || (q->key && cache.count(q->key)) ||
-                            nnz + q->nnz > 8 * cfg.batch_nnz)
+                            nnz + q->nnz > 8 * cfg.batch_nnz || nv + q->n > (int64_t(1) << 30))
                             break;
                         B.push_back(q);
                         need += q->est_bytes;
                         nnz += q->nnz;
+                        nv += q->n;
                     }
                     if (B.size() >= 2) {
                         if (resident + inflight + need > cfg.hbm_budget_bytes) evict_until(need);
