@@ -170,6 +170,12 @@ __device__ __forceinline__ int block_excl_scan_i(int v, int* sm, int* total) {
     return r;
 }
 
+// partners sorted per sub-chunk, per thread of the CTA kernel
+#ifndef TC_CTA_PER
+#define TC_CTA_PER 2
+#endif
+constexpr int kCtaPer = TC_CTA_PER;
+
 // Per-CTA partner scratch: the partners of one sub-chunk, sorted by list
 // length class (longest first), and the warp tasks cut from them.
 constexpr int kClasses = 16;
@@ -550,7 +556,7 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
     unsigned long long acc = 0;
-    constexpr int kPer = 2;  // partners per thread while sorting (pmax <= 2 * blockDim)
+    constexpr int kPer = kCtaPer;  // partners per thread while sorting (pmax <= kPer * blockDim)
     for (int c0 = pb; c0 < pe; c0 += pmax) {
         const int NP = min(pmax, pe - c0);
         if (tid < kClasses) sc.ccnt[tid] = 0;
@@ -637,9 +643,9 @@ static int cta_table_ints(int cap, int bitmap_bits) {
     return (std::max(8 * cap, bm) + 3) & ~3;  // whole 16-byte vectors (span clears)
 }
 
-// partners sorted per sub-chunk: 2 per thread
+// partners sorted per sub-chunk: kCtaPer per thread
 static size_t cta_smem_bytes(int u_ints, int threads) {
-    const int pmax = 2 * threads;
+    const int pmax = kCtaPer * threads;
     return (size_t)((u_ints + 1) & ~1) * sizeof(int) + (size_t)pmax * (sizeof(int64_t) + 2 * sizeof(int) + 1) +
            (3 * kClasses + 4 + 33) * sizeof(int) + 16;
 }
@@ -667,7 +673,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
     extern __shared__ __align__(16) int smem[];
     int* U = smem;
     CtaScratch sc;
-    const int pmax = 2 * blockDim.x;
+    const int pmax = kCtaPer * blockDim.x;
     sc.qb = reinterpret_cast<int64_t*>(smem + ((a.u_ints + 1) & ~1));
     sc.q = reinterpret_cast<int*>(sc.qb + pmax);
     sc.dq = sc.q + pmax;

@@ -190,3 +190,17 @@ def test_server_poll_and_timeout(B):
     with pytest.raises(B.TCError):
         srv.wait(tk, 10)  # released: unknown ticket
     srv.close()
+
+
+def test_server_fused_totals_without_per_vertex(B):
+    """Fused batches with per-vertex output off: every total exact."""
+    graphs = [gen.rmat(16, 16, seed=8)] + serving_mix(20, seed=6)
+    expect = [oracle.count(g.n, g.row_ptr, g.col)[0] for g in graphs]
+    srv = B.Server(slots=1, per_vertex=False, batch_graphs=16)
+    tickets = [srv.submit(g.n, g.row_ptr, g.col) for g in graphs]
+    res = [srv.wait(tk, 60000) for tk in tickets]
+    st = srv.stats()
+    srv.close()
+    for T, r in zip(expect, res):
+        assert r["status"] == 0 and r["total"] == T and r["per_vertex"] is None
+    assert st["batches"] >= 1
