@@ -222,31 +222,14 @@ struct Table {
     unsigned sbase;        // shared-memory address of the cell array (direct modes)
 };
 
-// Probe x; on a hit count it (per-vertex counter of x when PV) and return
-// true.
-template <int MODE, bool PV>
-__device__ __forceinline__ bool table_hit(const Table& t, int x) {
-    if (MODE == kModeDirect) {
-        const unsigned off = (unsigned)(x - t.lo);
-        if (off >= (unsigned)t.span) return false;
-        if (!t.cell[off]) return false;
-        if (PV) atomicAdd(reinterpret_cast<unsigned*>(t.cell + (off & ~1u)), 1u << ((off & 1u) * 16u));
-        return true;
-    } else if (MODE == kModeBitmap) {
-        const unsigned off = (unsigned)(x - t.lo);
-        if (off >= (unsigned)t.span) return false;
-        const unsigned word = t.bits[off >> 5];
-        const unsigned b = off & 31u;
-        if (!((word >> b) & 1u)) return false;
-        if (PV) atomicAdd(&t.cnts[(int)t.pre[off >> 5] + __popc(word & ((1u << b) - 1u))], 1);
-        return true;
-    } else {
-        const int h = MODE == kModeHash ? table_find_z(t.keys, t.logS, x)
-                                        : table_find<kProbeBsearch>(t.keys, t.logS, t.len, x);
-        if (h < 0) return false;
-        if (PV) atomicAdd(&t.cnts[h], 1);
-        return true;
-    }
+// Binary-search mode (probe = 2, vertex-id lists): find x in the sorted
+// segment; on a hit count it (per-vertex counter of x when PV) and return true.
+template <bool PV>
+__device__ __forceinline__ bool bsearch_hit(const Table& t, int x) {
+    const int h = table_find<kProbeBsearch>(t.keys, t.logS, t.len, x);
+    if (h < 0) return false;
+    if (PV) atomicAdd(&t.cnts[h], 1);
+    return true;
 }
 
 // Lanes per partner for a list-length class c (lists of 2^c .. 2^(c+1)-1
@@ -421,13 +404,14 @@ __device__ __forceinline__ unsigned long long warp_partners_vec(const CountArgs&
     return acc;
 }
 
-// Lane r of the G lanes that share one partner list (start qb, length dq in
-// L) probes the list's elements in the table, reading the list as aligned
-// 16-byte vectors r, r+G, ... (the lists are padded by 4 elements), kVec
-// vectors in flight.  Returns this lane's hits.
-template <int MODE, bool PV>
-__device__ __forceinline__ int probe_list(const Table& tb, const int32_t* __restrict__ L, int64_t qb, int dq, int r,
-                                          int G) {
+// Binary-search mode: lane r of the G lanes that share one partner list
+// (start qb, length dq in the unpadded vertex-id lists) probes the list's
+// elements, reading it as aligned 16-byte vectors r, r+G, ... (the lists are
+// padded by 4 elements at the end of the array), kVec vectors in flight, with
+// a bounds test per element.  Returns this lane's hits.
+template <bool PV>
+__device__ __forceinline__ int probe_list_bsearch(const Table& tb, const int32_t* __restrict__ L, int64_t qb, int dq,
+                                                  int r, int G) {
     const int s0 = (int)(qb & 3);
     const int4* __restrict__ lv = reinterpret_cast<const int4*>(L + (qb - s0));
     const int nv = (s0 + dq + 3) >> 2;
@@ -442,10 +426,10 @@ __device__ __forceinline__ int probe_list(const Table& tb, const int32_t* __rest
 #pragma unroll
         for (int u = 0; u < kVec; ++u) {
             const int j0 = 4 * (v0 + u * G) - s0;  // list position of w[u].x
-            if ((unsigned)(j0 + 0) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].x)) ++myc;
-            if ((unsigned)(j0 + 1) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].y)) ++myc;
-            if ((unsigned)(j0 + 2) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].z)) ++myc;
-            if ((unsigned)(j0 + 3) < (unsigned)dq && table_hit<MODE, PV>(tb, w[u].w)) ++myc;
+            if ((unsigned)(j0 + 0) < (unsigned)dq && bsearch_hit<PV>(tb, w[u].x)) ++myc;
+            if ((unsigned)(j0 + 1) < (unsigned)dq && bsearch_hit<PV>(tb, w[u].y)) ++myc;
+            if ((unsigned)(j0 + 2) < (unsigned)dq && bsearch_hit<PV>(tb, w[u].z)) ++myc;
+            if ((unsigned)(j0 + 3) < (unsigned)dq && bsearch_hit<PV>(tb, w[u].w)) ++myc;
         }
     }
     return myc;
@@ -622,8 +606,9 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             const int64_t qb = valid ? sc.qb[i] : 0;
             // level-partitioned lists (kSortedMin <= d+ <= kSortedMax) may stop below the table
             const int lev_exit = (dq >= kSortedMin && dq <= kSortedMax) ? tb.lev : INT_MAX;
-            int myc = MODE == kModeBsearch ? probe_list<MODE, PV>(tb, L, qb, dq, r, G)
-                                           : probe_list_padded<MODE, PV>(tb, L, qb, dq, r, G, lev_exit, (unsigned)a.n);
+            int myc;
+            if constexpr (MODE == kModeBsearch) myc = probe_list_bsearch<PV>(tb, L, qb, dq, r, G);
+            else myc = probe_list_padded<MODE, PV>(tb, L, qb, dq, r, G, lev_exit, (unsigned)a.n);
             for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
             if (r == 0 && valid && myc) {
                 acc += (unsigned long long)myc;
