@@ -178,14 +178,30 @@ def peaks():
         return 6800.0, "fallback"
 
 
+COUNT_SOURCES = ("paper_1804_06926_gb300/csrc/tc_count.cu", "paper_1804_06926_gb300/csrc/tc_internal.cuh")
+
+
+def code_digest(paths=COUNT_SOURCES):
+    """First 16 hex digits of sha256 over the code of the count kernels' sources
+    with // comments, trailing blanks and empty lines removed (a comment edit
+    leaves it unchanged, any code edit changes it)."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for p in paths:
+        for line in open(os.path.join(ROOT, p), encoding="utf-8"):
+            code = re.sub(r"//.*", "", line).rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel_tag):
     """DRAM bytes per launch of the timed kernel from the committed ncu summary,
-    if that summary was taken on the current source of the count kernels."""
-    import hashlib
+    if that summary was taken on the current code of the count kernels."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.ncu.txt")
-    src = os.path.join(ROOT, "paper_1804_06926_gb300", "csrc", "tc_count.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = code_digest()
         kv = {}
         for line in open(path):
             if ":" in line:

@@ -11,12 +11,15 @@
 //   k_count_small : one thread per source row u with d+(u) <= small_max;
 //                   sorted merge of N+(u) with each short N+(v).
 //   k_count_warp  : one warp per work item of a pivot with d+(p) <= warp_max;
-//                   N+(p) goes into a warp-private shared-memory table.
+//                   N+(p) goes into a warp-private rank-id hash table and the
+//                   lists of 32 partners q at a time are walked as one
+//                   flattened sequence of 16-byte vectors.
 //   k_count_cta   : one CTA per work item of a longer pivot list; the table
-//                   (one segment of N+(p)) is shared by all warps of the CTA.
-// In the table kernels every warp streams the lists of 32 partners q at a
-// time, flattened into one coalesced sequence of (partner, element) pairs,
-// and probes each element w of N+(q) in the table of N+(p).
+//                   (one segment of N+(p), a direct cell per rank id of its
+//                   span, a bitmap or a hash) is shared by all warps of the
+//                   CTA, which walk the partners' padded rank-id lists with
+//                   G lanes per partner by list-length class.
+// Every element w of N+(q) is probed in the table of N+(p).
 //
 // Per-vertex counts: triangle {p, q, w} with w in N+(p) and N+(q) is found
 // exactly once.  w is a key of the pivot's table, so its count accumulates in
@@ -144,13 +147,12 @@ constexpr int kVec = TC_CTA_VEC;  // 16-byte vector loads in flight per lane
 // ---------------------------------------------------------------------------
 // CTA-table kernel (persistent; items from a global queue)
 //
-// The whole CTA shares one table.  The partners of an item are taken up to
-// blockDim at a time; their lists are flattened into one sequence of E
-// elements and every warp walks an equal contiguous range of it, 32 elements
-// per window, so the work is balanced whatever the partner lengths are.  The
-// owner of each element comes from the partners whose lists start inside the
-// window (an OR-reduced bit mask over the next 32 list starts), as in
-// warp_partners; per-partner hit counts are summed per run of equal owners.
+// The whole CTA shares one table per item.  The item's partners are taken
+// kCtaPer * blockDim at a time, counting-sorted by list-length class in shared
+// memory and cut into warp tasks of 32/G partners of one class with G lanes
+// per partner (cta_partners); warps take tasks longest class first from a
+// shared counter, and each lane walks its part of the partner's padded
+// rank-id list (probe_list_padded).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int block_excl_scan_i(int v, int* sm, int* total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
