@@ -86,7 +86,7 @@ struct tc_ocsr {
     int32_t* rank = nullptr;    // [n] position of each vertex in (degree, id) order
     int32_t* perm = nullptr;    // [n] inverse of rank
     int32_t* colr = nullptr;    // colp relabelled to rank ids; row u at colr_row(rpp, u), padded with -1 to 4k entries
-    int2* rspan = nullptr;      // [n] smallest and largest rank id in each oriented row
+    int2* rspan = nullptr;      // [n] smallest and largest rank id of each row with d+ > warp_max (others unset)
     int64_t* prp = nullptr;     // [n+1] partner row offsets
     int32_t* pcol = nullptr;    // [m] partners (only the first n_pivot_edges used)
     tc::Item* items_warp = nullptr;
