@@ -207,7 +207,11 @@ constexpr int kModeDirect32 = 4; // one 32-bit cell per rank id, for spans up to
 // returned old value carries the marker, so a probe needs no separate load;
 // cells of rank ids that are not keys collect junk counts (at most one per
 // partner of the item, below the marker) and the whole span is cleared after
-// the item.
+// the item.  32-bit cells go one step further: a probe outside the span is
+// clamped to one of 32 dummy cells past it (span + lane, never marked), so
+// every probe is the same unpredicated atomic; the dummies collect junk
+// counts too (fewer than the item's probes, far below the marker) and are
+// cleared with the span.
 constexpr unsigned kMark32 = 0x80000000u;
 constexpr unsigned kMark16 = 0x8000u;
 
@@ -220,9 +224,32 @@ struct Table {
     unsigned short* cell;  // direct mode
     unsigned* cell32;      // direct mode, 32-bit cells
     int lo, span;
-    int lev;               // rank_level(n - smallest key): where walks of partitioned lists may stop
+    int xthr;              // walks of partitioned lists may stop at a batch whose lowest vector is below this
+    unsigned lim;          // span + lane: clamp of 32-bit direct probes
     unsigned sbase;        // shared-memory address of the cell array (direct modes)
 };
+
+// Smallest y >= 1 with rank_level(y) >= L (0: none below 2^32).  From octave 3
+// on every level is taken: level 8e + s first at y = (8 + s) << (e - 3).
+__device__ __forceinline__ unsigned level_min_y(int L) {
+    if (L <= 0) return 1u;
+    if (L >= kRankLevels) return 0u;
+    if (L >= 24) return (8u + (unsigned)(L & 7)) << ((L >> 3) - 3);
+    unsigned y = 1u;
+    while (rank_level(y) < L) ++y;  // y <= 8
+    return y;
+}
+
+// The walk of a level-partitioned list may stop after a vector whose largest
+// element x has rank_level(n - x) > L, L the level of the table's smallest key.
+// rank_level(n - x) does not increase with x, so for 0 <= x < n that test is
+// x < level_xthr(L, n): one compare per batch instead of a level computation.
+__device__ __forceinline__ int level_xthr(int L, long long n) {
+    const unsigned y = level_min_y(L + 1);
+    if (y == 0u) return INT_MIN;
+    const long long t = n - (long long)y + 1;
+    return t < (long long)INT_MIN ? INT_MIN : (int)t;
+}
 
 // Binary-search mode (probe = 2, vertex-id lists): find x in the sorted
 // segment; on a hit count it (per-vertex counter of x when PV) and return true.
@@ -447,7 +474,7 @@ __device__ __forceinline__ void red_shared_if(bool p, const void* addr, unsigned
         : "memory");
 }
 
-// The probe of a direct cell with per-vertex counts, as one predicated
+// The probe of a 16-bit direct cell with per-vertex counts, as one predicated
 // shared atomic: if off < span, add v to the 32-bit word at shared address
 // addr and return its old value, else return 0.  The span test is the
 // predicate itself, so a probe costs the offset, the address and the atomic.
@@ -466,8 +493,13 @@ __device__ __forceinline__ unsigned atom_probe(unsigned off, unsigned span, unsi
 template <int MODE, bool PV>
 __device__ __forceinline__ int probe1(const Table& t, int x) {
     if (MODE == kModeDirect32) {
+        if (PV) {
+            const unsigned off = min((unsigned)(x - t.lo), t.lim);
+            unsigned r;
+            asm volatile("atom.shared.add.u32 %0, [%1], 1;" : "=r"(r) : "r"(t.sbase + (off << 2)) : "memory");
+            return (int)(r >> 31);
+        }
         const unsigned off = (unsigned)(x - t.lo);
-        if (PV) return (int)(atom_probe(off, (unsigned)t.span, t.sbase + (off << 2), 1u) >> 31);
         const unsigned c = off < (unsigned)t.span ? t.cell32[off] : 0u;
         return c != 0u ? 1 : 0;
     } else if (MODE == kModeDirect) {
@@ -501,13 +533,13 @@ __device__ __forceinline__ int probe1(const Table& t, int x) {
 // probe_list for the padded rank-id rows: the list starts 16-byte aligned and
 // its last vector is filled up with -1, so every vector is probed whole.  The
 // lane walks vectors nv-1-r, nv-1-r-G, ... (top down).  For a list partitioned
-// by rank level, lev_exit is the level of the table's smallest key and the
-// walk stops after a batch whose lowest vector lies wholly in higher levels
-// (everything further down is below the table); lev_exit = INT_MAX walks the
-// whole list.
+// by rank level, x_exit is the table's level_xthr and the walk stops after a
+// batch whose lowest vector lies wholly in levels above that of the table's
+// smallest key (everything further down is below the table); x_exit = INT_MIN
+// walks the whole list.
 template <int MODE, bool PV>
 __device__ __forceinline__ int probe_list_padded(const Table& tb, const int32_t* __restrict__ L, int64_t qb, int dq,
-                                                 int r, int G, int lev_exit, unsigned n) {
+                                                 int r, int G, int x_exit) {
     const int4* __restrict__ lv = reinterpret_cast<const int4*>(L + qb);
     const int nv = (dq + 3) >> 2;
     int myc = 0;
@@ -523,7 +555,7 @@ __device__ __forceinline__ int probe_list_padded(const Table& tb, const int32_t*
             myc += probe1<MODE, PV>(tb, w[u].x) + probe1<MODE, PV>(tb, w[u].y) + probe1<MODE, PV>(tb, w[u].z) +
                    probe1<MODE, PV>(tb, w[u].w);
         const int4 t = w[kVec - 1];
-        if (rank_level(n - (unsigned)max(max(t.x, t.y), max(t.z, t.w))) > lev_exit) break;
+        if (max(max(t.x, t.y), max(t.z, t.w)) < x_exit) break;
     }
     return myc;
 }
@@ -607,10 +639,10 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             const int dq = valid ? sc.dq[i] : 0;
             const int64_t qb = valid ? sc.qb[i] : 0;
             // level-partitioned lists (kSortedMin <= d+ <= kSortedMax) may stop below the table
-            const int lev_exit = (dq >= kSortedMin && dq <= kSortedMax) ? tb.lev : INT_MAX;
+            const int x_exit = (dq >= kSortedMin && dq <= kSortedMax) ? tb.xthr : INT_MIN;
             int myc;
             if constexpr (MODE == kModeBsearch) myc = probe_list_bsearch<PV>(tb, L, qb, dq, r, G);
-            else myc = probe_list_padded<MODE, PV>(tb, L, qb, dq, r, G, lev_exit, (unsigned)a.n);
+            else myc = probe_list_padded<MODE, PV>(tb, L, qb, dq, r, G, x_exit);
             for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
             if (r == 0 && valid && myc) {
                 acc += (unsigned long long)myc;
@@ -714,7 +746,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
         const int len = (int)min((int64_t)a.cap, r1 - lb);
         Table tb{};
         tb.len = len;
-        tb.lev = INT_MAX;
+        tb.xthr = INT_MIN;
         tb.sbase = (unsigned)__cvta_generic_to_shared(U);
         int mode = PROBE == kProbeHash ? kModeHash : kModeBsearch;
         if (PROBE == kProbeHash && a.bitmap_bits > 0) {
@@ -733,7 +765,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
                 }
                 block_minmax(mn, mx, s_red);
             }
-            if (mx - mn < a.direct_span / 2 && mx - mn + 1 <= a.u_ints) {
+            if (mx - mn < a.direct_span / 2 && mx - mn + 1 + 32 <= a.u_ints) {  // + the dummy cells
                 mode = kModeDirect32;
                 tb.lo = mn;
                 tb.span = mx - mn + 1;
@@ -746,7 +778,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
                 tb.lo = mn;
                 tb.span = mx - mn + 1;
             }
-            if (mx >= 0) tb.lev = rank_level((unsigned)(a.n - mn));
+            if (mx >= 0) tb.xthr = level_xthr(rank_level((unsigned)(a.n - mn)), a.n);
+            tb.lim = (unsigned)tb.span + (unsigned)lane;
         }
         // the table region is all zeros here: every item resets what it set
         int nflush = 0;
@@ -816,7 +849,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
                 }
                 __syncthreads();
                 // clear the whole span (junk counts of non-keys included)
-                const int nz = mode == kModeDirect32 ? (tb.span + 3) >> 2 : (tb.span + 7) >> 3;
+                const int nz = mode == kModeDirect32 ? (tb.span + 32 + 3) >> 2 : (tb.span + 7) >> 3;
                 uint4* z = reinterpret_cast<uint4*>(U);
                 for (int i = threadIdx.x; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
             } else if (mode == kModeDirect32) {
