@@ -207,7 +207,8 @@ struct tc_server {
         }
         tc_status st = TC_OK;
         if (!o) {
-            // slot 0's releases are stream-ordered on slot 0; order this slot after them
+            // blocks that evictions released on slot 0's stream are reused here only
+            // after that release: the stream-ordered pool tracks the dependency
             tc_graph g{};
             g.n = r->n;
             g.nnz = r->nnz;
