@@ -88,7 +88,8 @@ typedef struct tc_config {
     int32_t probe;         /* 0/1 = open-addressing hash probe, 2 = binary search of the sorted list */
     int32_t cta_threads;   /* threads per CTA of the CTA-table kernel (64..1024); default 256 */
     int32_t chunk;         /* partners per work item of the warp-table class (CTA-table items take
-                              twice as many, at most 32767); default 512 */
+                              twice as many, at most 32767 and at most (2^31 - 1) / sqrt(2m));
+                              default 512 */
     int32_t bitmap_bits;   /* CTA items whose pivot list spans at most this many rank ids (vertices
                               renamed in (degree, id) order) probe a shared-memory bitmap instead of
                               the hash table; multiple of 32, <= 262144; default 131072; -1 = never */

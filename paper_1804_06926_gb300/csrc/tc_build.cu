@@ -200,7 +200,10 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ r
 // with the same offset).
 // ============================================================================
 // CTA work items carry this many times `chunk` partners (one table build and
-// flush serve them all; at most 32767 keeps the 16-bit direct cells exact)
+// flush serve them all; at most 32767 keeps the 16-bit direct cells exact, and
+// at most (2^31 - 1) / max d+ keeps every 32-bit direct cell of the count
+// kernel below its marker bit: an item probes at most partners x d+(pivot)
+// elements, since every partner's list is no longer than the pivot's)
 #ifndef TC_CTA_CHUNK_MUL
 #define TC_CTA_CHUNK_MUL 2
 #endif
@@ -753,13 +756,17 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     // upper bounds for the item lists (no host read-back of device sizes)
     const int64_t dmax = std::min<int64_t>(std::max<int64_t>(n, 1), isqrt_bound(2 * m));
     const int64_t chunk = tun.chunk, cap = tun.table_cap;
+    const int64_t chunk_c =
+        std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(chunk * TC_CTA_CHUNK_MUL, 32767),
+                                               ((int64_t(1) << 31) - 1) / std::max<int64_t>(dmax, 1)));
+    const int64_t chunk_min = std::min(chunk, chunk_c);  // partners of the shortest item of either list
     auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
     // warp items: sum over warp pivots of ceil(pc/chunk) <= #pivots + m/chunk
     o->items_warp_cap = std::min<int64_t>(n, m) + cdiv(m, chunk) + 1;
     // CTA items: sum of ceil(d/cap)*ceil(pc/chunk) <= sum (d/cap+1)(pc/chunk+1); d+ <= sqrt(2m)
     // (each of the d+(u) out-neighbours has degree >= d(u) >= d+(u)), sum pc <= m, sum d <= m,
     // and a CTA pivot has d > warp_max.
-    o->items_cta_cap = cdiv(dmax * m, cap * chunk) + cdiv(m, cap) + cdiv(m, chunk) + cdiv(m, tun.warp_max + 1) + 4;
+    o->items_cta_cap = cdiv(dmax * m, cap * chunk_min) + cdiv(m, cap) + cdiv(m, chunk_min) + cdiv(m, tun.warp_max + 1) + 4;
 
     int32_t* deg = nullptr;
     int32_t* pc = nullptr;
@@ -956,7 +963,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     if (n > 0) {
         PhaseScope ph(ctx, kPhItems, s);
         k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->dplus, o->prp, tun.warp_max, tun.table_cap, tun.chunk,
-                                                     (int)std::min<int64_t>((int64_t)tun.chunk * TC_CTA_CHUNK_MUL, 32767),
+                                                     (int)chunk_c,
                                                      o->items_warp, o->items_warp_cap, o->items_cta, o->items_cta_cap, o->dc);
         TC_LAUNCH(ctx);
     }
