@@ -47,7 +47,8 @@ typedef enum tc_status {
     TC_ERR_BUDGET = -4,          /* serving: request larger than the whole HBM budget */
     TC_ERR_TIMEOUT = -5,         /* a bounded wait gave up */
     TC_ERR_CUDA = -6,            /* any other CUDA runtime error (message in tc_last_error) */
-    TC_ERR_NOT_FOUND = -7        /* serving: unknown ticket */
+    TC_ERR_NOT_FOUND = -7,       /* serving: unknown ticket */
+    TC_ERR_DEVICE = -8           /* a device-side check failed (see tc_check); the results are not valid */
 } tc_status;
 
 /* tc_graph.flags / tc_batch.flags */
@@ -122,6 +123,24 @@ typedef struct tc_trace {
  * cfg may be NULL (all defaults).  Cheap; holds no graph memory. */
 tc_status tc_ctx_create(int device, const tc_config* cfg, tc_ctx** out);
 void tc_ctx_destroy(tc_ctx* ctx);
+/* Device-side checks.  The count kernels never spin without a bound and never
+ * access memory their invariants do not allow: when such a state is met the
+ * kernel skips the step and raises a bit of a per-device check word, which is
+ * sticky until tc_check reads it.  TC_DEVERR_PROBE: an open-addressing lookup
+ * or insert visited every slot of its table (tables are at most a quarter
+ * full, so this means a table left dirty).  The TC_DEBUG build of the library
+ * (compiled with -DTC_DEBUG=1) adds bounds checks: TC_DEVERR_BOUNDS, an index
+ * of a list, table or cell array out of range; TC_DEVERR_DIRTY, a table region
+ * not all zeros at the start of a work item. */
+#define TC_DEVERR_PROBE  0x1u
+#define TC_DEVERR_BOUNDS 0x2u
+#define TC_DEVERR_DIRTY  0x4u
+/* Synchronise `stream`, read and clear the check word of the current device;
+ * *bits (nullable) receives it.  TC_ERR_DEVICE if any bit was set, else TC_OK.
+ * tc_count and tc_count_batch with host outputs check it themselves (they
+ * synchronise anyway); with device outputs call tc_check after the counts. */
+tc_status tc_check(tc_ctx* ctx, uint32_t* bits, void* stream);
+
 /* One-line description of the last error on this context ("" if none). */
 const char* tc_last_error(const tc_ctx* ctx);
 /* Replace the tuning knobs (same meaning as in tc_ctx_create). */

@@ -109,6 +109,18 @@ def count_rows(n: int, rpp, colp, u_begin: int, u_end: int, stride: int = 1) -> 
     return int(_load().oracle_count_rows(n, rp.ctypes.data, c.ctypes.data, u_begin, u_end, stride, None))
 
 
+def count_rows_pv(n: int, rpp, colp, u_begin: int, u_end: int, stride: int = 1):
+    """(T_rows, t_rows): the triangles whose lowest-ranked vertex is one of the
+    rows u_begin, u_begin+stride, ... < u_end, and their per-vertex counts (a
+    private int64[n] array).  Summed over a partition of the rows they give the
+    whole graph's (T, t), so disjoint row subsets can run in separate processes."""
+    rp, c = _c64(rpp), _c32(colp)
+    t = np.zeros(n, np.int64)
+    T = _load().oracle_count_rows(n, rp.ctypes.data, c.ctypes.data, u_begin, u_end, stride,
+                                  t.ctypes.data if n > 0 else None)
+    return int(T), t
+
+
 def count(n: int, row_ptr, col, per_vertex: bool = True):
     """(T, t) for a simple undirected CSR: orient, then forward-count."""
     rpp, colp = orient(n, row_ptr, col)

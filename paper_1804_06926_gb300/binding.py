@@ -22,11 +22,13 @@ _lib = None
 TC_OK, TC_PENDING = 0, 1
 TC_ERR_INVALID_ARG, TC_ERR_INVALID_GRAPH, TC_ERR_OOM = -1, -2, -3
 TC_ERR_BUDGET, TC_ERR_TIMEOUT, TC_ERR_CUDA, TC_ERR_NOT_FOUND = -4, -5, -6, -7
+TC_ERR_DEVICE = -8
+TC_DEVERR_PROBE, TC_DEVERR_BOUNDS, TC_DEVERR_DIRTY = 0x1, 0x2, 0x4
 TC_IN_DEVICE, TC_IN_HOST, TC_VALIDATE = 0x0, 0x1, 0x2
 
 STATUS_NAMES = {0: "TC_OK", 1: "TC_PENDING", -1: "TC_ERR_INVALID_ARG", -2: "TC_ERR_INVALID_GRAPH",
                 -3: "TC_ERR_OOM", -4: "TC_ERR_BUDGET", -5: "TC_ERR_TIMEOUT", -6: "TC_ERR_CUDA",
-                -7: "TC_ERR_NOT_FOUND"}
+                -7: "TC_ERR_NOT_FOUND", -8: "TC_ERR_DEVICE"}
 
 
 class tc_graph(C.Structure):
@@ -87,6 +89,7 @@ _SIGS = {
     "tc_ctx_get_config": (C.c_int, [_vp, _P(tc_config)]),
     "tc_ctx_set_trace": (C.c_int, [_vp, C.c_int]),
     "tc_ctx_read_trace": (C.c_int, [_vp, _P(tc_trace)]),
+    "tc_check": (C.c_int, [_vp, _P(C.c_uint32), _vp]),
     "tc_build_oriented_csr": (C.c_int, [_vp, _P(tc_graph), _P(_vp), _vp]),
     "tc_count": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "tc_count_shard": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
@@ -296,6 +299,16 @@ class Context:
         h = _vp()
         _check(self, tc_build_oriented_csr(self.handle, C.byref(g), C.byref(h), _stream_ptr(stream)))
         return OCSR(self, h)
+
+    def check(self, stream=None) -> int:
+        """Synchronise, read and clear the device check word; raises TCError
+        (TC_ERR_DEVICE) if a device-side check failed since the last call."""
+        bits = C.c_uint32(0)
+        st = tc_check(self.handle, C.byref(bits), _stream_ptr(stream))
+        if st != TC_OK:
+            msg = tc_last_error(self.handle).decode()
+            raise TCError(st, msg)
+        return bits.value
 
     # -- count ------------------------------------------------------------
     def count(self, o: OCSR, total=None, per_vertex=None, stream=None):

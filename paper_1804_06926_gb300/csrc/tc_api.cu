@@ -137,8 +137,11 @@ static tc_status count_any(tc_ctx* ctx, const tc_ocsr* o, int64_t* totals, int64
     }
     if (h_tot) dev_free(dt, s);
     if (h_pv) dev_free(dpv, s);
-    e = cudaStreamSynchronize(s);
+    unsigned bits = 0u;
+    e = take_device_error(s, &bits);  // synchronises s
     if (st == TC_OK && e != cudaSuccess) st = cuda_err(ctx, e, "count: synchronise");
+    if (st == TC_OK && bits)
+        st = set_err(ctx, TC_ERR_DEVICE, "count: a device-side check failed (check word " + std::to_string(bits) + ")");
     return st;
 }
 

@@ -27,6 +27,8 @@
 // with a non-zero count; p one atomic per item.
 #include <algorithm>
 #include <climits>
+#include <cstdio>
+#include <string>
 
 #include "tc_internal.cuh"
 
@@ -60,63 +62,56 @@ struct CountArgs {
 constexpr int kProbeHash = 1;
 constexpr int kProbeBsearch = 2;
 
+// Device check word of the count kernels: a bit is raised (and the bad step
+// skipped) when a kernel meets a state its invariants exclude, instead of
+// spinning or touching memory out of bounds.  Sticky per device until
+// tc_check reads and clears it.
+__device__ unsigned g_tc_device_error = 0u;
+
+__device__ __forceinline__ void raise_error(unsigned bit) { atomicOr(&g_tc_device_error, bit); }
+
 __device__ __forceinline__ unsigned hslot(int x, int logS) {
     return ((unsigned)x * 0x9E3779B1u) >> (32 - logS);
 }
 
-__device__ __forceinline__ void table_insert(int* keys, int logS, int x) {
-    const unsigned mask = (1u << logS) - 1u;
-    unsigned h = hslot(x, logS);
-    while (true) {
-        const int prev = atomicCAS(&keys[h], -1, x);
-        if (prev == -1) return;
-        h = (h + 1u) & mask;
-    }
-}
-
-// Zero-encoded open addressing for the CTA tables: a slot holds x+1, 0 is
-// empty, so a table whose slots are reset after use is all zeros again.
+// Zero-encoded open addressing for the rank-id tables: a slot holds x+1, 0 is
+// empty, so a table whose slots are reset after use is all zeros again.  The
+// tables hold at most a quarter of their slots, so an insert always meets an
+// empty slot and a lookup of a missing key an empty slot too; both loops are
+// nevertheless bounded by the table size: a probe sequence that has visited
+// every slot (a table left dirty by an earlier item) gives up and raises
+// TC_DEVERR_PROBE.
 __device__ __forceinline__ void table_insert_z(int* keys, int logS, int x) {
     const unsigned mask = (1u << logS) - 1u;
     unsigned h = hslot(x, logS);
-    while (true) {
-        const int prev = atomicCAS(&keys[h], 0, x + 1);
-        if (prev == 0) return;
+    for (unsigned step = 0; step <= mask; ++step) {
+        if (atomicCAS(&keys[h], 0, x + 1) == 0) return;
         h = (h + 1u) & mask;
     }
+    raise_error(TC_DEVERR_PROBE);
 }
 
 __device__ __forceinline__ int table_find_z(const int* keys, int logS, int x) {
     const unsigned mask = (1u << logS) - 1u;
     unsigned h = hslot(x, logS);
-    while (true) {
+    for (unsigned step = 0; step <= mask; ++step) {
         const int k = keys[h];
         if (k == x + 1) return (int)h;
         if (k == 0) return -1;
         h = (h + 1u) & mask;
     }
+    raise_error(TC_DEVERR_PROBE);
+    return -1;
 }
 
-// slot of x, or -1
-template <int PROBE>
-__device__ __forceinline__ int table_find(const int* keys, int logS, int len, int x) {
-    if (PROBE == kProbeHash) {
-        const unsigned mask = (1u << logS) - 1u;
-        unsigned h = hslot(x, logS);
-        while (true) {
-            const int k = keys[h];
-            if (k == x) return (int)h;
-            if (k == -1) return -1;
-            h = (h + 1u) & mask;
-        }
-    } else {
-        int lo = 0, hi = len;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (keys[mid] < x) lo = mid + 1; else hi = mid;
-        }
-        return (lo < len && keys[lo] == x) ? lo : -1;
+// slot of x in the sorted keys[0, len), or -1 (binary search)
+__device__ __forceinline__ int table_find_sorted(const int* keys, int len, int x) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < x) lo = mid + 1; else hi = mid;
     }
+    return (lo < len && keys[lo] == x) ? lo : -1;
 }
 
 __device__ __forceinline__ int warp_incl_scan_i(int x) {
@@ -255,7 +250,7 @@ __device__ __forceinline__ int level_xthr(int L, long long n) {
 // segment; on a hit count it (per-vertex counter of x when PV) and return true.
 template <bool PV>
 __device__ __forceinline__ bool bsearch_hit(const Table& t, int x) {
-    const int h = table_find<kProbeBsearch>(t.keys, t.logS, t.len, x);
+    const int h = table_find_sorted(t.keys, t.len, x);
     if (h < 0) return false;
     if (PV) atomicAdd(&t.cnts[h], 1);
     return true;
@@ -320,7 +315,7 @@ __device__ __forceinline__ unsigned long long warp_partners(const CountArgs& a, 
             for (int u = 0; u < kUnroll; ++u) {
                 bool hit = false;
                 if (in[u]) {
-                    const int h = table_find<PROBE>(keys, logS, len, w[u]);
+                    const int h = table_find_sorted(keys, len, w[u]);
                     if (h >= 0) {
                         hit = true;
                         if (PV) atomicAdd(&cnts[h], 1);
@@ -1153,4 +1148,35 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     return TC_OK;
 }
 
+cudaError_t take_device_error(cudaStream_t s, unsigned* bits) {
+    static const unsigned zero = 0u;
+    unsigned h = 0u;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&h, g_tc_device_error, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbolAsync(g_tc_device_error, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *bits = h;
+    return e;
+}
+
+cudaError_t peek_device_error_async(unsigned* h_pinned, cudaStream_t s) {
+    if (!h_pinned) return cudaErrorInvalidValue;
+    return cudaMemcpyFromSymbolAsync(h_pinned, g_tc_device_error, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
+}
+
 }  // namespace tc
+
+extern "C" tc_status tc_check(tc_ctx* ctx, uint32_t* bits, void* stream) {
+    if (!ctx) return TC_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    unsigned b = 0u;
+    cudaError_t e = tc::take_device_error((cudaStream_t)stream, &b);
+    if (bits) *bits = b;
+    if (e != cudaSuccess) return tc::cuda_err(ctx, e, "tc_check");
+    if (b) return tc::set_err(ctx, TC_ERR_DEVICE, "device check failed (check word 0x" + [](unsigned v) {
+                                  char buf[16];
+                                  snprintf(buf, sizeof buf, "%x", v);
+                                  return std::string(buf);
+                              }(b) + "): the results of the counts since the last check are not valid");
+    return TC_OK;
+}

@@ -168,4 +168,9 @@ tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t npairs, const int32_t* sr
 tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals,
                        unsigned long long* per_vertex, cudaStream_t s, int shard = 0, int nshards = 1);
 
+// Read and clear the device check word of the current device (synchronises s).
+cudaError_t take_device_error(cudaStream_t s, unsigned* bits);
+// Enqueue a copy of the check word (not cleared) into pinned host memory on s.
+cudaError_t peek_device_error_async(unsigned* h_pinned, cudaStream_t s);
+
 }  // namespace tc

@@ -88,6 +88,7 @@ struct Slot {
     unsigned long long* d_total = nullptr;
     unsigned long long* d_pv = nullptr;
     int64_t d_pv_cap = 0;
+    unsigned* h_err = nullptr;   // pinned copy of the device check word, read at retire
 };
 
 struct CacheEntry {
@@ -232,6 +233,7 @@ struct tc_server {
             cudaMemcpyAsync(r->h_total, sl.d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
             if (cfg.per_vertex && r->n > 0)
                 cudaMemcpyAsync(r->h_pv, sl.d_pv, sizeof(int64_t) * r->n, cudaMemcpyDeviceToHost, s);
+            tc::peek_device_error_async(sl.h_err, s);
             cudaEventRecord(sl.ev, s);
         }
         if (st != TC_OK) {
@@ -319,6 +321,7 @@ struct tc_server {
             cudaMemcpyAsync(b.h_tot, b.d_tot, sizeof(int64_t) * b.G, cudaMemcpyDeviceToHost, s);
             if (cfg.per_vertex && b.N > 0)
                 cudaMemcpyAsync(b.h_pv, b.d_pv, sizeof(int64_t) * b.N, cudaMemcpyDeviceToHost, s);
+            tc::peek_device_error_async(sl.h_err, s);
             cudaEventRecord(sl.ev, s);
         }
         if (st != TC_OK) {
@@ -350,7 +353,7 @@ struct tc_server {
             r->h_pv = nullptr;
             free_inputs(r);
             inflight -= r->est_bytes;
-            finish(r, TC_OK);
+            finish(r, *sl.h_err ? TC_ERR_DEVICE : TC_OK);
         }
         tc_ocsr_release(sl.o, sl.stream);
         sl.o = nullptr;
@@ -384,7 +387,7 @@ struct tc_server {
         }
         sl.req = nullptr;
         sl.o = nullptr;
-        finish(r, TC_OK);
+        finish(r, *sl.h_err ? TC_ERR_DEVICE : TC_OK);
     }
 
     void loop() {
@@ -501,8 +504,11 @@ tc_status tc_server_create(const tc_server_config* cfg, const tc_config* tuning,
         cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         cudaMalloc((void**)&sl.d_total, sizeof(int64_t));
+        if (cudaHostAlloc((void**)&sl.h_err, sizeof(unsigned), cudaHostAllocPortable) == cudaSuccess) *sl.h_err = 0u;
     }
-    if (cudaGetLastError() != cudaSuccess) {
+    bool pinned = true;
+    for (auto& sl : s->slots) pinned = pinned && sl.h_err;
+    if (cudaGetLastError() != cudaSuccess || !pinned) {
         tc_server_destroy(s);
         return TC_ERR_CUDA;
     }
@@ -526,6 +532,7 @@ void tc_server_destroy(tc_server* s) {
         if (sl.d_total) cudaFree(sl.d_total);
         if (sl.d_pv) cudaFree(sl.d_pv);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.h_err) cudaFreeHost(sl.h_err);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
     for (auto& kv : s->reqs) {

@@ -1,13 +1,13 @@
 """Parity at the benchmark sizes, in the launch configuration bench.py times
 (default tc_config, per-vertex counts on).
 
-* R-MAT scale 22: the oracle's total T (forward algorithm over strided row
-  subsets in a spawn-started process pool) must equal the GPU total; sampled
-  vertices' t(v) from the definition (adjacent pairs among N(v)) must equal
-  the GPU's; sum t = 3T.
+* R-MAT scale 22: the oracle's T and every one of the 4,194,304 t(v)
+  (forward algorithm over strided row subsets in a spawn-started process
+  pool, each worker with a private per-vertex array, summed) must equal the
+  GPU's bit for bit (the hubs, whose lists fill the CTA tables, included).
 * 4096 x 4096 road-like grid: full oracle, every t(v) bit-exact.
-* 4096 Barabasi-Albert graphs in one batched pass: every per-graph total
-  against the oracle, per-vertex counts of sampled graphs bit-exact.
+* 4096 Barabasi-Albert graphs in one batched pass: every per-graph total and
+  every per-vertex count of every graph against the oracle.
 """
 from __future__ import annotations
 
@@ -31,11 +31,12 @@ _CTX = mp.get_context("spawn")
 def _rows_worker(args):
     path, n, r, stride = args
     d = np.load(path, mmap_mode="r")
-    return oracle.count_rows(n, np.asarray(d["rpp"]), np.asarray(d["colp"]), r, n, stride)
+    return oracle.count_rows_pv(n, np.asarray(d["rpp"]), np.asarray(d["colp"]), r, n, stride)
 
 
-def oracle_total_parallel(n, row_ptr, col, procs=None):
-    """T from the oracle: orient once, then count strided row subsets in parallel."""
+def oracle_counts_parallel(n, row_ptr, col, procs=None):
+    """(T, t) from the oracle: orient once, then count strided row subsets in
+    parallel, each with its own per-vertex array; the parts add up exactly."""
     rpp, colp = oracle.orient(n, row_ptr, col)
     procs = procs or max(1, min(16, os.cpu_count() or 1))
     with tempfile.TemporaryDirectory() as tmp:
@@ -43,19 +44,24 @@ def oracle_total_parallel(n, row_ptr, col, procs=None):
         np.savez(path, rpp=rpp, colp=colp)
         with _CTX.Pool(procs) as pool:
             parts = pool.map(_rows_worker, [(path, n, r, procs) for r in range(procs)])
-    return int(sum(parts))
+    T = int(sum(p[0] for p in parts))
+    t = np.zeros(n, np.int64)
+    for p in parts:
+        t += p[1]
+    return T, t
 
 
 def _batch_worker(args):
     path, lo, hi = args
     d = np.load(path, mmap_mode="r")
     vo, eo, rp, col = d["vo"], d["eo"], d["rp"], d["col"]
-    out = []
+    Ts, ts = [], []
     for i in range(lo, hi):
         v0, v1, e0, e1 = int(vo[i]), int(vo[i + 1]), int(eo[i]), int(eo[i + 1])
-        T, _ = oracle.count(v1 - v0, np.asarray(rp[v0:v1 + 1]) - e0, np.asarray(col[e0:e1]), per_vertex=False)
-        out.append(T)
-    return out
+        T, t = oracle.count(v1 - v0, np.asarray(rp[v0:v1 + 1]) - e0, np.asarray(col[e0:e1]))
+        Ts.append(T)
+        ts.append(t)
+    return Ts, (np.concatenate(ts) if ts else np.zeros(0, np.int64))
 
 
 @pytest.fixture(scope="module")
@@ -76,19 +82,14 @@ def gpu_count(ctx, g):
     return int(tot.item()), pv.cpu().numpy()
 
 
-def test_rmat22_total_and_sampled_vertices(B):
+def test_rmat22_every_vertex(B):
     g = gen.rmat(22, 16, seed=0)
     ctx = B.Context(0)
     T, t = gpu_count(ctx, g)
+    To, to = oracle_counts_parallel(g.n, g.row_ptr, g.col)
+    assert T == To
+    np.testing.assert_array_equal(t, to)
     assert int(t.sum()) == 3 * T
-    assert T == oracle_total_parallel(g.n, g.row_ptr, g.col)
-    deg = np.diff(g.row_ptr)
-    rng = np.random.default_rng(0)
-    cand = np.nonzero((deg > 0) & (deg <= 3000))[0]
-    sample = list(rng.choice(cand, 300, replace=False))
-    sample += list(np.argsort(deg)[-20000:][::2000])  # a few high-degree vertices as well
-    for v in sample:
-        assert oracle.vertex_triangles(g.n, g.row_ptr, g.col, int(v)) == t[v], v
 
 
 def test_grid4096_full(B):
@@ -117,9 +118,41 @@ def test_ba_batch4096(B):
         cuts = np.linspace(0, b.G, procs + 1).astype(int)
         with _CTX.Pool(procs) as pool:
             parts = pool.map(_batch_worker, [(path, int(cuts[i]), int(cuts[i + 1])) for i in range(procs)])
-    T_ref = np.array([x for p in parts for x in p], np.int64)
+    T_ref = np.array([x for p in parts for x in p[0]], np.int64)
+    t_ref = np.concatenate([p[1] for p in parts])
     np.testing.assert_array_equal(T_gpu, T_ref)
-    for i in (0, 1, 777, 2048, 4095):
-        gi = b.graph(i)
-        _, t = oracle.count(gi.n, gi.row_ptr, gi.col)
-        np.testing.assert_array_equal(pv_gpu[b.vtx_off[i]:b.vtx_off[i + 1]], t)
+    assert t_ref.shape == pv_gpu.shape
+    np.testing.assert_array_equal(pv_gpu, t_ref)
+
+
+def test_serving_mix_rmat10_to_20(B):
+    """The serving workload's request mix at its full size range: one R-MAT
+    graph of every scale 10..20 (edge factor 16) and BA graphs as in the batch
+    workload, submitted together to an 8-slot server (40 GB budget, small
+    requests fused into batches, some keys cached and repeated) and one at a
+    time to a 1-slot server; every total and every t(v) equals the oracle's
+    both ways."""
+    rng = np.random.default_rng(5)
+    graphs = [gen.rmat(s, 16, seed=100 + s) for s in range(10, 21)]
+    graphs += [gen.ba(int(rng.integers(100, 20001)), int(rng.integers(2, 17)), seed=int(rng.integers(1 << 30)))
+               for _ in range(8)]
+    expect = [oracle_counts_parallel(g.n, g.row_ptr, g.col) if g.m > 1_000_000 else oracle.count(g.n, g.row_ptr, g.col)
+              for g in graphs]
+    srv = B.Server(slots=1, per_vertex=True, batch_graphs=1)
+    alone = [srv.wait(srv.submit(g.n, g.row_ptr, g.col), 600000) for g in graphs]
+    srv.close()
+    order = list(rng.permutation(len(graphs))) * 2
+    srv = B.Server(slots=8, per_vertex=True, hbm_budget_bytes=40 << 30)
+    tickets = [srv.submit(graphs[i].n, graphs[i].row_ptr, graphs[i].col, key=(1 + int(i)) if k % 3 == 0 else 0)
+               for k, i in enumerate(order)]
+    mixed = [srv.wait(tk, 600000) for tk in tickets]
+    st = srv.stats()
+    srv.close()
+    for (T, t), a in zip(expect, alone):
+        assert a["status"] == 0 and a["total"] == T
+        np.testing.assert_array_equal(a["per_vertex"], t)
+    for i, m in zip(order, mixed):
+        T, t = expect[i]
+        assert m["status"] == 0 and m["total"] == T
+        np.testing.assert_array_equal(m["per_vertex"], t)
+    assert st["finished"] == len(order) and st["peak_inflight"] >= 2

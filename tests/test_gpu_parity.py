@@ -61,6 +61,8 @@ def assert_parity(ctx, g, **kw):
     assert Tg == T
     if kw.get("per_vertex", True):
         np.testing.assert_array_equal(tg, t)
+    # no device-side check (bounded probes) fired during the count
+    assert ctx.check() == 0
     return T
 
 

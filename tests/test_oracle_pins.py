@@ -224,6 +224,14 @@ def test_invariants(seed):
     assert int(t.sum()) == 3 * T
     # strided row subsets partition the count
     assert sum(oracle.count_rows(g.n, rpp, colp, r, g.n, 4) for r in range(4)) == T
+    # ... and so do their per-vertex counts
+    parts = [oracle.count_rows_pv(g.n, rpp, colp, r, g.n, 3) for r in range(3)]
+    assert sum(p[0] for p in parts) == T
+    assert (sum(p[1] for p in parts) == t).all()
+    # a per-vertex row subset agrees with the definition at its lowest vertex:
+    # every triangle of row u (u lowest-ranked) contains u
+    Tu, tu = oracle.count_rows_pv(g.n, rpp, colp, 5, 6)
+    assert tu[5] == Tu and int(tu.sum()) == 3 * Tu
     # relabelling the vertices permutes t and keeps T
     perm = np.random.default_rng(seed).permutation(g.n).astype(np.int32)
     src = perm[np.repeat(np.arange(g.n), np.diff(g.row_ptr))]
