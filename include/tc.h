@@ -89,7 +89,7 @@ typedef struct tc_config {
     int32_t probe;         /* 0/1 = open-addressing hash probe, 2 = binary search of the sorted list */
     int32_t cta_threads;   /* threads per CTA of the CTA-table kernel (64..1024); default 256 */
     int32_t chunk;         /* partners per work item of the warp-table class (CTA-table items take
-                              twice as many, at most 32767 and at most (2^31 - 1) / sqrt(2m));
+                              twice as many, at most 32767 and at most (2^31 - 1) / (sqrt(2m) + 4));
                               default 512 */
     int32_t bitmap_bits;   /* CTA items whose pivot list spans at most this many rank ids (vertices
                               renamed in (degree, id) order) probe a shared-memory bitmap instead of
@@ -243,9 +243,8 @@ void tc_ocsr_release(tc_ocsr* o, void* stream);
 /* ---- oriented CSR without device allocation --------------------------------
  * The paper has no counterpart; this serves callers that cannot allocate
  * device memory while running: serving loops with a latency budget (cudaMalloc
- * and cudaFree may synchronise the device), processes whose HBM is already
- * reserved in full by another allocator, and code running while a framework
- * captures the stream into a graph that must hold no allocation nodes.
+ * and cudaFree may synchronise the device) and processes whose HBM is already
+ * reserved in full by another allocator.
  *
  * tc_orient_noalloc writes the same oriented CSR as tc_build_oriented_csr
  * followed by tc_ocsr_copy: rpp_out[n+1] (int64) and colp_out[nnz/2] (int32),
@@ -256,9 +255,11 @@ void tc_ocsr_release(tc_ocsr* o, void* stream);
  * library, which every GPU that loads the library keeps until the process
  * exits; that caps n at TC_NOALLOC_MAX_VERTICES, and larger graphs get
  * TC_ERR_INVALID_ARG (use tc_build_oriented_csr for them).  The first call on
- * a device looks the array's address up (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  All calls share the array: calls
- * whose work overlaps on the GPU race and must be serialised by the caller. */
+ * a device looks the array's address up (cudaGetSymbolAddress) and keeps it for
+ * the life of the process, so make that first call before any stream capture,
+ * and do not call it again after cudaDeviceReset on that device (the array
+ * then moves).  All calls share the array: calls whose work overlaps on the
+ * GPU race and must be serialised by the caller. */
 #define TC_NOALLOC_MAX_VERTICES (1LL << 24)
 tc_status tc_orient_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
                             int64_t* rpp_out, int32_t* colp_out, void* stream);

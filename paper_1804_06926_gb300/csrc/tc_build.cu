@@ -200,10 +200,12 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ r
 // with the same offset).
 // ============================================================================
 // CTA work items carry this many times `chunk` partners (one table build and
-// flush serve them all; at most 32767 keeps the 16-bit direct cells exact, and
-// at most (2^31 - 1) / max d+ keeps every 32-bit direct cell of the count
-// kernel below its marker bit: an item probes at most partners x d+(pivot)
-// elements, since every partner's list is no longer than the pivot's)
+// flush serve them all).  At most 32767 partners keep the 16-bit direct cells
+// exact.  At most (2^31 - 1) / (max d+ + 3) partners keep every 32-bit direct
+// cell of the count kernel below its marker bit: a cell inside the table's
+// span gains at most one count per partner (a list holds each id once), and
+// the 32 dummy cells past the span take the probes that fall outside it,
+// padding included, at most partners x (max d+ + 3) elements in all.
 #ifndef TC_CTA_CHUNK_MUL
 #define TC_CTA_CHUNK_MUL 2
 #endif
@@ -758,7 +760,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     const int64_t chunk = tun.chunk, cap = tun.table_cap;
     const int64_t chunk_c =
         std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(chunk * TC_CTA_CHUNK_MUL, 32767),
-                                               ((int64_t(1) << 31) - 1) / std::max<int64_t>(dmax, 1)));
+                                               ((int64_t(1) << 31) - 1) / (dmax + 3)));
     const int64_t chunk_min = std::min(chunk, chunk_c);  // partners of the shortest item of either list
     auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
     // warp items: sum over warp pivots of ceil(pc/chunk) <= #pivots + m/chunk

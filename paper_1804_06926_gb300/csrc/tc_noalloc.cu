@@ -3,10 +3,9 @@
 //
 // Some callers cannot allocate device memory once they are running: serving
 // loops with a latency budget (cudaMalloc and cudaFree may synchronise the
-// device), processes whose HBM is already fully reserved by another
-// allocator, and code that runs while a framework captures the stream into a
-// graph that must not contain allocation nodes.  This entry point lets them
-// build the oriented CSR with buffers they own.
+// device) and processes whose HBM is already fully reserved by another
+// allocator.  This entry point lets them build the oriented CSR with buffers
+// they own.
 //
 // Its only scratch is the tile-sum array of the exclusive scan over the
 // per-row kept counts.  It lives in a file-scope __device__ array of fixed
@@ -36,7 +35,8 @@ std::mutex g_setup_mu;
 long long* g_scratch[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// per device with that device current and kept for the life of the process
+// (a cudaDeviceReset of the device would move the array; the header says so).
 cudaError_t scratch_ptr(int dev, long long** out) {
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!g_scratch[dev]) {

@@ -34,16 +34,14 @@ def graph_ranges(edge_off, world: int):
     return [(cuts[r], cuts[r + 1]) for r in range(world)]
 
 
-def row_ranges(work, world: int):
-    """Contiguous row ranges [lo, hi) per rank with about equal summed work
-    (work[u] >= 0 per source row), the partition used to shard one graph."""
-    w = np.asarray(work, dtype=np.float64)
-    pre = np.concatenate([[0.0], np.cumsum(w)])
-    total = pre[-1]
-    cuts = [0] + [int(np.searchsorted(pre, total * r / world, side="left")) for r in range(1, world)] + [w.shape[0]]
-    for i in range(1, len(cuts)):
-        cuts[i] = min(max(cuts[i], cuts[i - 1]), w.shape[0])
-    return [(cuts[r], cuts[r + 1]) for r in range(world)]
+def shard_bounds(n_all: int, shard: int, nshards: int):
+    """[lo, hi) of a work list of n_all units that shard `shard` of `nshards`
+    takes: the same integer arithmetic the count kernels apply to each of their
+    work lists (CTA items, warp items, small-class source rows) under
+    tc_count_shard, so that the shards cover every unit exactly once."""
+    if nshards < 1 or not 0 <= shard < nshards:
+        raise ValueError("shard must be in [0, nshards)")
+    return n_all * shard // nshards, n_all * (shard + 1) // nshards
 
 
 def allreduce_counts(total, per_vertex=None, group=None):
