@@ -98,7 +98,18 @@ typedef struct tc_config {
                               rank id (presence and hits in one probe; 32-bit cells up to half this
                               span, 16-bit above); <= 16384; default 16384;
                               -1 = never (needs bitmap_bits > 0) */
-    int32_t reserved[8];
+    int32_t merge_ratio;   /* degree-ratio switch between the two intersection strategies of Sec. 4.2.2:
+                              an oriented edge that is not thread-merged, whose longer list has at most
+                              merge_max elements and whose ratio r = max(d+)/min(d+) is at most
+                              merge_ratio/100, is intersected by a warp-cooperative merge path over
+                              both sorted lists (balanced lists); every other edge probes its pivot's
+                              table (skewed lists).  Percent, >= 100; default 0 = no merge class */
+    int32_t merge_max;     /* see merge_ratio; 16..4096, default 256 */
+    int32_t stage;         /* CTA-table kernel: 1 = the partner lists walked by 4 or more lanes are
+                              staged into shared memory by the copy engine (cp.async.bulk), one batch
+                              ahead of the probing; 0 (default) or -1 = every lane loads its own
+                              vectors (faster on GB300: the small copies wait longer than the loads) */
+    int32_t reserved[5];
 } tc_config;
 
 typedef struct tc_ctx tc_ctx;
@@ -107,11 +118,12 @@ typedef struct tc_ocsr tc_ocsr;
 /* Tracing: CUDA events around each phase, recorded on the stream the phase
  * runs on, plus a count of the library's kernel launches.  Off by default;
  * never active inside a CUDA-graph capture. */
-#define TC_TRACE_PHASES 16
+#define TC_TRACE_PHASES 20
 enum {
     TC_PH_DEGREE = 0, TC_PH_VALIDATE, TC_PH_ORIENT_COUNT, TC_PH_ORIENT_SCAN, TC_PH_ORIENT_SCATTER,
     TC_PH_PIVOT_COUNT, TC_PH_PIVOT_SCAN, TC_PH_PIVOT_SCATTER, TC_PH_ITEMS, TC_PH_COUNT_SMALL,
-    TC_PH_COUNT_WARP, TC_PH_COUNT_CTA, TC_PH_EDGE_SORT, TC_PH_COUNT_INIT, TC_PH_RANK, TC_PH_ROW_SORT
+    TC_PH_COUNT_WARP, TC_PH_COUNT_CTA, TC_PH_EDGE_SORT, TC_PH_COUNT_INIT, TC_PH_RANK, TC_PH_ROW_SORT,
+    TC_PH_COUNT_MERGE
 };
 typedef struct tc_trace {
     int64_t launches;                        /* kernel launches since the last read */
@@ -128,13 +140,16 @@ void tc_ctx_destroy(tc_ctx* ctx);
  * kernel skips the step and raises a bit of a per-device check word, which is
  * sticky until tc_check reads it.  TC_DEVERR_PROBE: an open-addressing lookup
  * or insert visited every slot of its table (tables are at most a quarter
- * full, so this means a table left dirty).  The TC_DEBUG build of the library
+ * full, so this means a table left dirty).  TC_DEVERR_WAIT: a wait for a
+ * staged copy of partner lists gave up (about a second); the warp went on
+ * without staging.  The TC_DEBUG build of the library
  * (compiled with -DTC_DEBUG=1) adds bounds checks: TC_DEVERR_BOUNDS, an index
  * of a list, table or cell array out of range; TC_DEVERR_DIRTY, a table region
  * not all zeros at the start of a work item. */
 #define TC_DEVERR_PROBE  0x1u
 #define TC_DEVERR_BOUNDS 0x2u
 #define TC_DEVERR_DIRTY  0x4u
+#define TC_DEVERR_WAIT   0x8u  /* a wait for a staged copy of the count kernel gave up (about 1 s) */
 /* Synchronise `stream`, read and clear the check word of the current device;
  * *bits (nullable) receives it.  TC_ERR_DEVICE if any bit was set, else TC_OK.
  * tc_count and tc_count_batch with host outputs check it themselves (they

@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build", platform.machine())
 LIB = os.path.join(HERE, "libtc.so")
 STAMP = LIB + ".arch"
+# The TC_DEBUG build: every count kernel checks its indexes and table invariants,
+# raises a bit of the device check word (tc_check) and skips the bad access.
+DEBUG_LIB = os.path.join(HERE, "libtc_debug.so")
 SOURCES = ["tc_build.cu", "tc_count.cu", "tc_sort.cu", "tc_api.cu", "tc_serve.cu", "tc_noalloc.cu", "tc_metrics.cu", "tc_support.cu", "tc_labels.cu"]
 HEADERS = [os.path.join(CSRC, "tc_internal.cuh"), os.path.join(ROOT, "include", "tc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,16 +40,21 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link libtc.so (or, with debug=True, libtc_debug.so)."""
+    bdir = os.path.join(BUILD, "debug") if debug else BUILD
+    lib = DEBUG_LIB if debug else LIB
+    stamp = lib + ".arch"
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
+    flags = NVCC_FLAGS + (["-DTC_DEBUG=1"] if debug else [])
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
-            jobs.append([cc] + NVCC_FLAGS + ["-I", os.path.join(ROOT, "include"), "-c", s, "-o", o])
+            jobs.append([cc] + flags + ["-I", os.path.join(ROOT, "include"), "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -58,12 +66,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs) or not arch_ok(STAMP):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or jobs or _stale(lib, objs) or not arch_ok(stamp):
+        tmp = lib + f".{os.getpid()}.tmp"
         run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
-        os.replace(tmp, LIB)
-        write_stamp(STAMP)
-    return LIB
+        os.replace(tmp, lib)
+        write_stamp(stamp)
+    return lib
 
 
 def arch_ok(stamp: str) -> bool:

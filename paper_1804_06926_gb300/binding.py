@@ -23,7 +23,7 @@ TC_OK, TC_PENDING = 0, 1
 TC_ERR_INVALID_ARG, TC_ERR_INVALID_GRAPH, TC_ERR_OOM = -1, -2, -3
 TC_ERR_BUDGET, TC_ERR_TIMEOUT, TC_ERR_CUDA, TC_ERR_NOT_FOUND = -4, -5, -6, -7
 TC_ERR_DEVICE = -8
-TC_DEVERR_PROBE, TC_DEVERR_BOUNDS, TC_DEVERR_DIRTY = 0x1, 0x2, 0x4
+TC_DEVERR_PROBE, TC_DEVERR_BOUNDS, TC_DEVERR_DIRTY, TC_DEVERR_WAIT = 0x1, 0x2, 0x4, 0x8
 TC_IN_DEVICE, TC_IN_HOST, TC_VALIDATE = 0x0, 0x1, 0x2
 
 STATUS_NAMES = {0: "TC_OK", 1: "TC_PENDING", -1: "TC_ERR_INVALID_ARG", -2: "TC_ERR_INVALID_GRAPH",
@@ -39,7 +39,8 @@ class tc_graph(C.Structure):
 class tc_config(C.Structure):
     _fields_ = [("small_max", C.c_int32), ("warp_max", C.c_int32), ("table_cap", C.c_int32),
                 ("probe", C.c_int32), ("cta_threads", C.c_int32), ("chunk", C.c_int32),
-                ("bitmap_bits", C.c_int32), ("direct_span", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("bitmap_bits", C.c_int32), ("direct_span", C.c_int32), ("merge_ratio", C.c_int32),
+                ("merge_max", C.c_int32), ("stage", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class tc_ocsr_view(C.Structure):
@@ -66,11 +67,11 @@ class tc_result(C.Structure):
 
 TRACE_PHASES = ("degree", "validate", "orient_count", "orient_scan", "orient_scatter", "pivot_count",
                 "pivot_scan", "pivot_scatter", "items", "count_small", "count_warp", "count_cta", "edge_sort",
-                "count_init", "rank", "row_sort")
+                "count_init", "rank", "row_sort", "count_merge")
 
 
 class tc_trace(C.Structure):
-    _fields_ = [("launches", C.c_int64), ("phase_ms", C.c_double * 16), ("phase_calls", C.c_int32 * 16)]
+    _fields_ = [("launches", C.c_int64), ("phase_ms", C.c_double * 20), ("phase_calls", C.c_int32 * 20)]
 
 
 class tc_server_stats(C.Structure):
@@ -121,17 +122,24 @@ TC_NOALLOC_MAX_VERTICES = 1 << 24
 EXPORTS = tuple(_SIGS)
 
 
+def debug_requested() -> bool:
+    """TC_LIBRARY=debug selects the TC_DEBUG build (bounds-checked kernels)."""
+    return os.environ.get("TC_LIBRARY", "") == "debug"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.DEBUG_LIB if debug_requested() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load libtc.so (building it with nvcc if it is missing or stale)."""
+    """Load libtc.so, or libtc_debug.so when TC_LIBRARY=debug (building it with
+    nvcc if it is missing or stale)."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        dbg = debug_requested()
+        path = _build.DEBUG_LIB if dbg else _build.LIB
         if build_if_missing:
-            path = _build.build()
+            path = _build.build(debug=dbg)
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build()")
         lib = C.CDLL(path)

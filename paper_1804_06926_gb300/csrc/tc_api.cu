@@ -5,6 +5,8 @@
 #include <cstring>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -39,7 +41,15 @@ static cudaEvent_t get_event(tc_ctx* c) {
     return e;
 }
 
+// NVTX range names of the phases (host-side ranges around each phase's
+// launches; a profiler that records NVTX shows them beside the kernels)
+static const char* const kPhaseNames[kNumPhases] = {
+    "tc.degree",        "tc.validate",   "tc.orient_count", "tc.orient_scan", "tc.orient_scatter", "tc.pivot_count",
+    "tc.pivot_scan",    "tc.pivot_scatter", "tc.items",     "tc.count_small", "tc.count_warp",     "tc.count_cta",
+    "tc.edge_sort",     "tc.count_init", "tc.rank",         "tc.row_sort",    "tc.count_merge"};
+
 PhaseScope::PhaseScope(tc_ctx* c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
+    nvtxRangePushA(id >= 0 && id < kNumPhases ? kPhaseNames[id] : "tc.phase");
     if (c && c->trace) {
         a = get_event(c);
         cudaEventRecord(a, s);
@@ -52,6 +62,7 @@ PhaseScope::~PhaseScope() {
         cudaEventRecord(b, s);
         c->recs.push_back({id, a, b});
     }
+    nvtxRangePop();
 }
 
 // Defaults, then TC_SMALL_MAX / TC_WARP_MAX / TC_TABLE_CAP / TC_PROBE /
@@ -71,6 +82,9 @@ static void apply_config(Tuning& t, const tc_config* c) {
     env("TC_CHUNK", t.chunk);
     env("TC_BITMAP_BITS", t.bitmap_bits);
     env("TC_DIRECT_SPAN", t.direct_span);
+    env("TC_MERGE_RATIO", t.merge_ratio);
+    env("TC_MERGE_MAX", t.merge_max);
+    env("TC_STAGE", t.stage);
     if (!c) return;
     if (c->small_max > 0) t.small_max = c->small_max;
     if (c->small_max < 0) t.small_max = 0;  // negative disables the thread-per-edge class
@@ -83,6 +97,10 @@ static void apply_config(Tuning& t, const tc_config* c) {
     if (c->bitmap_bits < 0) t.bitmap_bits = 0;
     if (c->direct_span > 0) t.direct_span = c->direct_span;
     if (c->direct_span < 0) t.direct_span = 0;
+    if (c->merge_ratio > 0) t.merge_ratio = c->merge_ratio;
+    if (c->merge_ratio < 0) t.merge_ratio = 0;
+    if (c->merge_max > 0) t.merge_max = c->merge_max;
+    if (c->stage != 0) t.stage = c->stage > 0 ? 1 : 0;
 }
 
 static bool config_ok(const Tuning& t) {
@@ -91,7 +109,9 @@ static bool config_ok(const Tuning& t) {
            pow2(t.table_cap) && t.table_cap >= 16 && t.table_cap <= 4096 &&
            (t.probe == 1 || t.probe == 2) && t.cta_threads >= 64 && t.cta_threads <= 1024 &&
            t.cta_threads % 32 == 0 && t.chunk >= 1 && t.chunk <= 32768 && t.bitmap_bits >= 0 &&
-           t.bitmap_bits <= 262144 && t.bitmap_bits % 32 == 0 && t.direct_span >= 0 && t.direct_span <= 16384;
+           t.bitmap_bits <= 262144 && t.bitmap_bits % 32 == 0 && t.direct_span >= 0 && t.direct_span <= 16384 &&
+           (t.merge_ratio == 0 || (t.merge_ratio >= 100 && t.merge_ratio <= 1000000)) && t.merge_max >= 16 &&
+           t.merge_max <= 4096 && t.stage >= 0 && t.stage <= 1;
 }
 
 static bool is_host_ptr(const void* p) {
@@ -148,7 +168,7 @@ static tc_status count_any(tc_ctx* ctx, const tc_ocsr* o, int64_t* totals, int64
 static void release_ocsr(tc_ocsr* o, cudaStream_t s, bool async) {
     if (!o) return;
     void* ptrs[] = {o->rpp,  o->colp, o->dplus,      o->deg, o->rank,      o->perm, o->colr,     o->rspan,
-                    o->prp, o->pcol, o->items_warp, o->items_cta, o->dc,   o->row_graph};
+                    o->prp, o->pcol, o->items_warp, o->items_cta, o->dc,   o->row_graph, o->medge};
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(o->device);
@@ -255,6 +275,9 @@ tc_status tc_ctx_get_config(const tc_ctx* ctx, tc_config* out) {
     out->chunk = ctx->tun.chunk;
     out->bitmap_bits = ctx->tun.bitmap_bits;
     out->direct_span = ctx->tun.direct_span;
+    out->merge_ratio = ctx->tun.merge_ratio;
+    out->merge_max = ctx->tun.merge_max;
+    out->stage = ctx->tun.stage;
     return TC_OK;
 }
 

@@ -343,11 +343,14 @@ __global__ void k_popc(const unsigned* __restrict__ mask, int64_t nw, int32_t* _
 // read them as whole aligned 16-byte vectors.
 // ============================================================================
 // Partition classes of an oriented edge (u, v) with a = d+(u), b = d+(v); see a-4 below.
-enum { kSkip = 0, kSmall = 1, kPivot = 2 };
+enum { kSkip = 0, kSmall = 1, kPivot = 2, kMerge = 3 };
 
-__device__ __forceinline__ int edge_class(int a, int b, int small_max) {
+__device__ __forceinline__ int edge_class(int a, int b, int small_max, int merge_ratio, int merge_max) {
     if (a <= 1 || b == 0) return kSkip;
-    if (max(a, b) <= small_max) return kSmall;
+    const int hi = max(a, b), lo = min(a, b);
+    if (hi <= small_max) return kSmall;
+    // the degree-ratio switch: balanced lists of moderate length merge
+    if (merge_ratio > 0 && hi <= merge_max && 100ll * hi <= (long long)merge_ratio * lo) return kMerge;
     return kPivot;
 }
 
@@ -389,9 +392,11 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(i
 }
 
 // rpp[u] = kept entries before row u, and d+(u) (and its maximum)
+// (and (rank(u), d+(u)) packed, so that the scatter gathers both of a
+// neighbour with one 8-byte load)
 __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned* __restrict__ keep,
-                       const int64_t* __restrict__ kpre, int64_t* __restrict__ rpp, int32_t* __restrict__ dplus,
-                       int* __restrict__ max_dplus) {
+                       const int64_t* __restrict__ kpre, const int32_t* __restrict__ rank, int64_t* __restrict__ rpp,
+                       int32_t* __restrict__ dplus, int2* __restrict__ rd2, int* __restrict__ max_dplus) {
     int mx = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = bits_before(keep, kpre, rp[u]);
@@ -399,6 +404,7 @@ __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned
         if (u < n) {
             const int d = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
             dplus[u] = d;
+            rd2[u] = make_int2(rank[u], d);
             mx = max(mx, d);
         }
     }
@@ -409,10 +415,12 @@ __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned
 template <bool BATCH>
 __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient_scatter(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                                const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                               const int32_t* __restrict__ rank, const int32_t* __restrict__ row_graph,
+                                                               const int2* __restrict__ rd2, const int32_t* __restrict__ row_graph,
                                                                const int64_t* __restrict__ vtx_off, const unsigned* __restrict__ keep,
                                                                const int64_t* __restrict__ kpre, const int64_t* __restrict__ rpp,
-                                                               const int32_t* __restrict__ dp, int small_max,
+                                                               int small_max,
+                                                               int merge_ratio, int merge_max, int2* __restrict__ medge,
+                                                               int64_t medge_cap,
                                                                int32_t* __restrict__ colp, int32_t* __restrict__ colr,
                                                                unsigned* __restrict__ umask,
                                                                unsigned* __restrict__ vmask, int32_t* __restrict__ nv,
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
         for (int k = threadIdx.x; k < nr; k += blockDim.x) {
             const int64_t u = i0 + k;
             S.du[k] = (int)((rpp[u] + 3 * u + 3) & 3);
-            S.cs[k] = dp[u];
+            S.cs[k] = rd2[u].y;
         }
         __syncthreads();
         // all loads of the tile first: keep words and lists, then the rank gathers
@@ -454,15 +462,17 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
         int bb[kMpIpt];
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
-            rr[q] = kw[q] ? rank[vv[q]] : 0;
-            bb[q] = kw[q] ? dp[vv[q]] : 0;
+            const int2 rv = kw[q] ? rd2[vv[q]] : make_int2(0, 0);
+            rr[q] = rv.x;
+            bb[q] = rv.y;
         }
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
             const bool valid = e < ne;
             int64_t pos = 0;
-            bool pu = false, pv = false;
+            bool pu = false, pv = false, mg = false;
+            int mu = 0;
             if (valid) {
                 const int k = S.row[e];
                 if (kw[q]) {
@@ -472,13 +482,25 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                     colr[pos + 3 * (i0 + k) + 3 - S.du[k]] = rr[q];
                     // a-4 classification of the oriented edge (u, v) at position pos
                     const int a = S.cs[k], b = bb[q];
-                    const int cls = edge_class(a, b, small_max);
+                    const int cls = edge_class(a, b, small_max, merge_ratio, merge_max);
                     pu = cls == kPivot && a >= b;
                     pv = cls == kPivot && a < b;
+                    mg = cls == kMerge;
+                    mu = (int)(i0 + k);
                     my_small += cls == kSmall;
                     my_piv += pu || pv;
                     if (pv) atomicAdd(&nv[vv[q]], 1);
                 }
+            }
+            // merge-class edges are appended to their list, one atomic per warp
+            const unsigned mb = __ballot_sync(0xffffffffu, mg);
+            if (mb) {
+                const int lead = __ffs(mb) - 1;
+                unsigned long long base = 0;
+                if (lane == lead) base = atomicAdd(&dc->n_merge_edges, (unsigned long long)__popc(mb));
+                base = __shfl_sync(0xffffffffu, base, lead);
+                const unsigned long long at = base + __popc(mb & ((1u << lane) - 1u));
+                if (mg && at < (unsigned long long)medge_cap) medge[at] = make_int2(mu, vv[q]);
             }
             // the warp's kept entries sit at consecutive positions: one bit
             // pattern per mask, placed at the first kept entry's position
@@ -602,6 +624,10 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const 
 // Every oriented edge (u, v) with a = d+(u), b = d+(v) falls in one class:
 //   skip  : a <= 1 or b == 0 (N+(u) = {v} or N+(v) empty: no common vertex);
 //   small : max(a, b) <= small_max -> one thread merges the two lists;
+//   merge : (when the degree-ratio switch is on) max(a, b) <= merge_max and
+//           max(a, b) <= merge_ratio/100 * min(a, b): balanced lists, merged
+//           by one warp along the merge path of both (the paper's TwoLarge
+//           intersection of Sec. 4.2.2); appended to the merge edge list;
 //   pivot : otherwise.  The endpoint with the longer list is the pivot p (u
 //           on ties), the other is the partner q.  The pivot's list becomes a
 //           shared-memory table and the partner's (shorter) list is streamed
@@ -618,15 +644,20 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const 
 // and nV) is done by k_orient_scatter as it places each kept entry.
 // ============================================================================
 
-// prp[p] = U(rpp[p]) + Vpre(p), p = 0 .. n
+// prp[p] = U(rpp[p]) + Vpre(p), p = 0 .. n; vtop[p] = prp[p+1], the end of
+// p's V-part, which the scatter counts down from
 __global__ void k_pivot_offsets(int64_t n, const int64_t* __restrict__ rpp, const unsigned* __restrict__ umask,
                                 const int64_t* __restrict__ upre, const int64_t* __restrict__ vpre,
-                                int64_t* __restrict__ prp) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += (int64_t)gridDim.x * blockDim.x)
-        prp[p] = bits_before(umask, upre, rpp[p]) + vpre[p];
+                                int64_t* __restrict__ prp, unsigned long long* __restrict__ vtop) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = bits_before(umask, upre, rpp[p]) + vpre[p];
+        prp[p] = o;
+        if (p > 0) vtop[p - 1] = (unsigned long long)o;
+    }
 }
 
-// nv[p] counts down from nV(p) while p's V-part is filled.
+// vtop[p] counts down from the end of p's V-part while it is filled (one
+// returned 64-bit atomic gives the slot).
 #ifndef TC_PSCATTER_MIN_BLOCKS
 #define TC_PSCATTER_MIN_BLOCKS 1
 #endif
@@ -634,7 +665,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_sc
                                                               const int64_t* __restrict__ rpp, const int32_t* __restrict__ colp,
                                                               const unsigned* __restrict__ umask, const unsigned* __restrict__ vmask,
                                                               const int64_t* __restrict__ upre, const int64_t* __restrict__ vpre,
-                                                              const int64_t* __restrict__ prp, int32_t* __restrict__ nv,
+                                                              unsigned long long* __restrict__ vtop,
                                                               int32_t* __restrict__ pcol) {
     __shared__ MpTile<false> S;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -673,7 +704,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_sc
             const int64_t g = j0 + e;
             dst[q] = -1;
             if (cu[q] >= 0) dst[q] = upre[g >> 5] + cu[q] + vpre[i0 + S.row[e]];
-            else if ((pvm >> q) & 1u) dst[q] = prp[(int64_t)vv[q] + 1] - atomicSub(&nv[vv[q]], 1);
+            else if ((pvm >> q) & 1u) dst[q] = (int64_t)atomicAdd(&vtop[vv[q]], ~0ull) - 1;
         }
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
@@ -685,10 +716,12 @@ __global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_sc
     }
 }
 
-// Work items per pivot.  Warp class (d+(p) <= warp_max): one item per chunk of
-// partners.  CTA class: one item per (segment of the pivot list, chunk_c
-// partners); a segment holds at most table_cap keys.
-__global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restrict__ dp, const int64_t* __restrict__ prp,
+// Work items per pivot, pivots taken in descending rank order.  Warp class
+// (d+(p) <= warp_max): one item per chunk of partners.  CTA class: one item per
+// (segment of the pivot list, chunk_c partners); a segment holds at most
+// table_cap keys.
+__global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ dp,
+                                               const int64_t* __restrict__ prp,
                                                int warp_max, int table_cap, int chunk, int chunk_c,
                                                Item* __restrict__ iw, int64_t iw_cap,
                                                Item* __restrict__ ic, int64_t ic_cap,
@@ -696,7 +729,10 @@ __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restr
     __shared__ long long sm[33];
     __shared__ unsigned long long s_bw, s_bc;
     for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < n; t0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = t0 + threadIdx.x;
+        // pivots in descending rank order: pivots of similar rank share many
+        // partners, so the partner lists that concurrent items stream stay in L2
+        const int64_t r = t0 + threadIdx.x;
+        const int64_t p = r < n ? perm[n - 1 - r] : n;
         int pcnt = 0, d = 0;
         if (p < n) { pcnt = (int)(prp[p + 1] - prp[p]); d = dp[p]; }
         const bool is_warp = d <= warp_max;
@@ -790,6 +826,10 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     A((void**)&o->items_warp, sizeof(Item) * o->items_warp_cap);
     A((void**)&o->items_cta, sizeof(Item) * o->items_cta_cap);
     A((void**)&o->dc, sizeof(DevCounters));
+    if (tun.merge_ratio > 0) {  // the merge class holds at most every oriented edge
+        o->medge_cap = std::max<int64_t>(m, 1);
+        A((void**)&o->medge, sizeof(int2) * o->medge_cap);
+    }
     if (batch) A((void**)&o->row_graph, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&o->deg, sizeof(int32_t) * std::max<int64_t>(n, 1));
     A((void**)&pc, sizeof(int32_t) * std::max<int64_t>(n, 1));
@@ -800,7 +840,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     }
     deg = o->deg;
     o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 9 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
-                         + (batch ? sizeof(int32_t) * n : 0));
+                         + (batch ? sizeof(int32_t) * n : 0) + sizeof(int2) * o->medge_cap);
     cudaMemsetAsync(o->dc, 0, sizeof(DevCounters), s);
 
     const int ns = ctx->num_sms;
@@ -862,6 +902,8 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     unsigned *keep = nullptr, *umask = nullptr, *vmask = nullptr;
     int32_t* wpc = nullptr;
     int64_t *kpre = nullptr, *upre = nullptr, *vpre = nullptr;
+    int2* rd2 = nullptr;
+    unsigned long long* vtop = nullptr;
     void* wtmp = nullptr;
     const size_t wtb = scan_tmp_bytes(std::max(kw, std::max(uw, n)));
     auto B = [&](void** p, size_t b) {
@@ -875,10 +917,13 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     B((void**)&kpre, sizeof(int64_t) * (kw + 1));
     B((void**)&upre, sizeof(int64_t) * (uw + 1));
     B((void**)&vpre, sizeof(int64_t) * n1);
+    B((void**)&rd2, sizeof(int2) * std::max<int64_t>(n, 1));
+    B((void**)&vtop, sizeof(unsigned long long) * std::max<int64_t>(n, 1));
     B(&wtmp, wtb);
     auto free_tmp = [&]() {
         dev_free(coord, s); dev_free(keep, s); dev_free(umask, s); dev_free(vmask, s); dev_free(wpc, s);
         dev_free(kpre, s); dev_free(upre, s); dev_free(vpre, s); dev_free(wtmp, s);
+        dev_free(rd2, s); dev_free(vtop, s);
         dev_free(pc, s);
     };
     if (e != cudaSuccess) {
@@ -906,7 +951,8 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         k_popc<<<grid_for(kw, 256, ns), 256, 0, s>>>(keep, kw, wpc);
         scan_i32_to_i64(wpc, kpre, kw, wtmp, wtb, s);
         // row offsets and d+
-        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rpp, o->dplus, &o->dc->max_dplus);
+        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rank, o->rpp, o->dplus, rd2,
+                                                        &o->dc->max_dplus);
         ctx->launches += 5;
     }
     {
@@ -919,12 +965,14 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         cudaMemsetAsync(vmask, 0, sizeof(unsigned) * uw, s);
         if (nt1 > 0) {
             if (batch)
-                k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, o->row_graph, vtx_off, keep, kpre,
-                                                                 o->rpp, o->dplus, tun.small_max, o->colp, o->colr,
+                k_orient_scatter<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, rd2, o->row_graph, vtx_off, keep, kpre,
+                                                                 o->rpp, tun.small_max, tun.merge_ratio, tun.merge_max,
+                                                                 o->medge, o->medge_cap, o->colp, o->colr,
                                                                  umask, vmask, pc, o->dc);
             else
-                k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, o->rank, nullptr, nullptr, keep, kpre,
-                                                                  o->rpp, o->dplus, tun.small_max, o->colp, o->colr,
+                k_orient_scatter<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, rd2, nullptr, nullptr, keep, kpre,
+                                                                  o->rpp, tun.small_max, tun.merge_ratio, tun.merge_max,
+                                                                  o->medge, o->medge_cap, o->colp, o->colr,
                                                                   umask, vmask, pc, o->dc);
             TC_LAUNCH(ctx);
         }
@@ -950,21 +998,22 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         k_popc<<<grid_for(uw, 256, ns), 256, 0, s>>>(umask, uw, wpc);
         scan_i32_to_i64(wpc, upre, uw, wtmp, wtb, s);
         scan_i32_to_i64(pc, vpre, n, wtmp, wtb, s);
-        k_pivot_offsets<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, o->rpp, umask, upre, vpre, o->prp);
+        k_pivot_offsets<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, o->rpp, umask, upre, vpre, o->prp, vtop);
         ctx->launches += 8;
     }
     {
         PhaseScope ph(ctx, kPhPivotScatter, s);
         if (nt2 > 0) {
-            k_pivot_scatter<<<g2, kMpThreads, 0, s>>>(n, nt2, coord, o->rpp, o->colp, umask, vmask, upre, vpre, o->prp, pc, o->pcol);
+            k_pivot_scatter<<<g2, kMpThreads, 0, s>>>(n, nt2, coord, o->rpp, o->colp, umask, vmask, upre, vpre, vtop, o->pcol);
             TC_LAUNCH(ctx);
         }
     }
     dev_free(coord, s); dev_free(keep, s); dev_free(umask, s); dev_free(vmask, s); dev_free(wpc, s);
     dev_free(kpre, s); dev_free(upre, s); dev_free(vpre, s); dev_free(wtmp, s);
+    dev_free(rd2, s); dev_free(vtop, s);
     if (n > 0) {
         PhaseScope ph(ctx, kPhItems, s);
-        k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->dplus, o->prp, tun.warp_max, tun.table_cap, tun.chunk,
+        k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->perm, o->dplus, o->prp, tun.warp_max, tun.table_cap, tun.chunk,
                                                      (int)chunk_c,
                                                      o->items_warp, o->items_warp_cap, o->items_cta, o->items_cta_cap, o->dc);
         TC_LAUNCH(ctx);

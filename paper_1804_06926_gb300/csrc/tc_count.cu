@@ -57,6 +57,7 @@ struct CountArgs {
     int shard, nshards;           // this launch covers shard `shard` of `nshards` equal parts of the work
     int cap;                      // keys per table segment
     int small_max;
+    int64_t colr_len, colp_len;   // entries allocated for colr and colp (debug bounds checks)
 };
 
 constexpr int kProbeHash = 1;
@@ -69,6 +70,20 @@ constexpr int kProbeBsearch = 2;
 __device__ unsigned g_tc_device_error = 0u;
 
 __device__ __forceinline__ void raise_error(unsigned bit) { atomicOr(&g_tc_device_error, bit); }
+
+// Bounds and invariant checks of the TC_DEBUG build (-DTC_DEBUG=1): a failed
+// check raises its bit of the check word and the guarded access is skipped.
+// In the release build every check is the constant true.
+#ifndef TC_DEBUG
+#define TC_DEBUG 0
+#endif
+__device__ __forceinline__ bool dbg_ok(bool cond, unsigned bit) {
+    if (TC_DEBUG && !cond) {
+        raise_error(bit);
+        return false;
+    }
+    return true;
+}
 
 __device__ __forceinline__ unsigned hslot(int x, int logS) {
     return ((unsigned)x * 0x9E3779B1u) >> (32 - logS);
@@ -220,8 +235,11 @@ struct Table {
     unsigned* cell32;      // direct mode, 32-bit cells
     int lo, span;
     int xthr;              // walks of partitioned lists may stop at a batch whose lowest vector is below this
+    int64_t llen;          // entries of the list array walked (debug checks)
     unsigned lim;          // span + lane: clamp of 32-bit direct probes
     unsigned sbase;        // shared-memory address of the cell array (direct modes)
+    int ucap;              // ints of the table region (debug checks)
+    int wmax;              // words of the bitmap (debug checks)
 };
 
 // Smallest y >= 1 with rank_level(y) >= L (0: none below 2^32).  From octave 3
@@ -397,7 +415,8 @@ __device__ __forceinline__ unsigned long long warp_partners_vec(const CountArgs&
                 P += __popc(M);
                 const int64_t bj = __shfl_sync(FULL, base, j & 31);
                 const int k = k0 + 32 * u + lane;
-                w[u] = k < tot ? lv[bj + k] : make_int4(-1, -1, -1, -1);
+                w[u] = (k < tot && dbg_ok((bj + k) * 4 + 3 < a.colr_len, TC_DEVERR_BOUNDS)) ? lv[bj + k]
+                                                                                             : make_int4(-1, -1, -1, -1);
             }
 #pragma unroll
             for (int u = 0; u < kWarpVec; ++u) {
@@ -445,7 +464,8 @@ __device__ __forceinline__ int probe_list_bsearch(const Table& tb, const int32_t
 #pragma unroll
         for (int u = 0; u < kVec; ++u) {
             const int vv = v0 + u * G;
-            w[u] = vv < nv ? lv[vv] : make_int4(0, 0, 0, 0);
+            w[u] = (vv < nv && dbg_ok(qb - s0 + 4ll * vv + 3 < tb.llen, TC_DEVERR_BOUNDS)) ? lv[vv]
+                                                                                           : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < kVec; ++u) {
@@ -490,6 +510,7 @@ __device__ __forceinline__ int probe1(const Table& t, int x) {
     if (MODE == kModeDirect32) {
         if (PV) {
             const unsigned off = min((unsigned)(x - t.lo), t.lim);
+            if (!dbg_ok(off < (unsigned)t.ucap, TC_DEVERR_BOUNDS)) return 0;
             unsigned r;
             asm volatile("atom.shared.add.u32 %0, [%1], 1;" : "=r"(r) : "r"(t.sbase + (off << 2)) : "memory");
             return (int)(r >> 31);
@@ -499,6 +520,7 @@ __device__ __forceinline__ int probe1(const Table& t, int x) {
         return c != 0u ? 1 : 0;
     } else if (MODE == kModeDirect) {
         const unsigned off = (unsigned)(x - t.lo);
+        if (!dbg_ok(off >= (unsigned)t.span || (off >> 1) < (unsigned)t.ucap, TC_DEVERR_BOUNDS)) return 0;
         if (PV) {
             const unsigned sh = (off & 1u) << 4;
             return (int)((atom_probe(off, (unsigned)t.span, t.sbase + ((off << 1) & ~3u), 1u << sh) >> (15u + sh)) & 1u);
@@ -507,7 +529,7 @@ __device__ __forceinline__ int probe1(const Table& t, int x) {
         return c != 0u ? 1 : 0;
     } else if (MODE == kModeBitmap) {
         const unsigned off = (unsigned)(x - t.lo);
-        const bool in = off < (unsigned)t.span;
+        const bool in = off < (unsigned)t.span && dbg_ok((off >> 5) < (unsigned)t.wmax, TC_DEVERR_BOUNDS);
         const unsigned word = in ? t.bits[off >> 5] : 0u;
         const unsigned b = off & 31u;
         const bool hit = (word >> b) & 1u;
@@ -519,7 +541,7 @@ __device__ __forceinline__ int probe1(const Table& t, int x) {
     } else {
         if (x < 0) return 0;
         const int h = table_find_z(t.keys, t.logS, x);
-        if (h < 0) return 0;
+        if (h < 0 || !dbg_ok(h < t.ucap / 2, TC_DEVERR_BOUNDS)) return 0;
         if (PV) atomicAdd(&t.cnts[h], 1);
         return 1;
     }
@@ -543,7 +565,8 @@ __device__ __forceinline__ int probe_list_padded(const Table& tb, const int32_t*
 #pragma unroll
         for (int u = 0; u < kVec; ++u) {
             const int vv = v0 - u * G;
-            w[u] = vv >= 0 ? lv[vv] : make_int4(-1, -1, -1, -1);
+            w[u] = (vv >= 0 && dbg_ok(qb + 4ll * vv + 3 < tb.llen, TC_DEVERR_BOUNDS)) ? lv[vv]
+                                                                                      : make_int4(-1, -1, -1, -1);
         }
 #pragma unroll
         for (int u = 0; u < kVec; ++u)
@@ -551,6 +574,152 @@ __device__ __forceinline__ int probe_list_padded(const Table& tb, const int32_t*
                    probe1<MODE, PV>(tb, w[u].w);
         const int4 t = w[kVec - 1];
         if (max(max(t.x, t.y), max(t.z, t.w)) < x_exit) break;
+    }
+    return myc;
+}
+
+// ---------------------------------------------------------------------------
+// Staged partner lists (CTA-table kernel, lists of >= 4 lanes per partner)
+//
+// A warp task covers 32/G partners with G lanes each; the lanes of one partner
+// walk its padded rank-id list top down in batches of 4 vectors per lane, so
+// batch b of the task is, for every partner, the 4G vectors below the ones of
+// batch b-1: at most 32 x 4 = 128 vectors (2 KB) in all.  Instead of loading them
+// itself, the warp has lane 0 copy batch b+1 of every live partner from
+// global into one of its two shared-memory slots with cp.async.bulk (one copy
+// per partner, completing on the slot's mbarrier) before it probes batch b
+// from the other slot, so the copy engine moves the lists while the lanes
+// probe.  Each warp owns its two slots and two mbarriers and waits for its
+// copies in the order it issued them, so a slot's phase parity always names
+// the copy waited for.  A partner whose lowest vector of a batch lies wholly
+// below the table is not copied again (everything further down is below it).
+// ---------------------------------------------------------------------------
+constexpr int kSlotVec = 128;                    // vectors (16 B) per staging slot
+static_assert(32 * kVec <= kSlotVec, "a batch of a warp task fills at most one slot");
+constexpr long long kWaitCycles = 2000000000ll;  // about one second at 2 GHz
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned addr, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(addr),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned addr, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void* src, unsigned bytes, unsigned mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+struct StageCtx {
+    int4* buf;          // this warp's two slots (2 x kSlotVec vectors)
+    unsigned bar;       // shared address of this warp's two mbarriers (8 bytes apart)
+    unsigned issued;    // batches issued so far: batch k uses slot k & 1, phase parity (k >> 1) & 1
+    bool failed;        // a wait gave up (TC_DEVERR_WAIT raised); the warp stops staging
+};
+
+// Lane 0 copies batch b of every live partner of the task into the next slot.
+// All lanes take part (the partners' descriptors are broadcast from their
+// first lanes); lane 0 alone issues the copies and the transaction count.
+__device__ __forceinline__ void stage_issue(const int32_t* __restrict__ colr, StageCtx& st, int G, int ppt,
+                                            int64_t qb, int nv, bool live, int b) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int W = kVec * G;
+    const unsigned slot = st.issued & 1u;
+    const unsigned bar = st.bar + 8u * slot;
+    const unsigned dst0 = smem_u32(st.buf + (size_t)slot * kSlotVec);
+    unsigned bytes = 0;
+    __syncwarp();  // every lane is done with the batch this slot held before
+    for (int sp = 0; sp < ppt; ++sp) {
+        const int64_t q_b = __shfl_sync(FULL, qb, sp * G);
+        const int q_nv = __shfl_sync(FULL, nv, sp * G);
+        const int q_live = __shfl_sync(FULL, live ? 1 : 0, sp * G);
+        const int hi = q_nv - b * W, lo = max(0, hi - W);
+        if (lane == 0 && q_live && hi > 0) {
+            const unsigned nb = (unsigned)(hi - lo) * 16u;
+            bulk_copy_g2s(dst0 + (unsigned)(sp * W) * 16u, colr + q_b + 4ll * lo, nb, bar);
+            bytes += nb;
+        }
+    }
+    if (lane == 0) mbar_arrive_tx(bar, bytes);
+    st.issued += 1;
+}
+
+// Every lane waits for batch k itself (so that each observes the copy's
+// completion before reading the slot); bounded: past kWaitCycles the lane gives
+// up, and the warp stops staging if any lane gave up (a warp-uniform decision).
+__device__ __forceinline__ void stage_wait(StageCtx& st, unsigned k) {
+    const unsigned bar = st.bar + 8u * (k & 1u), par = (k >> 1) & 1u;
+    bool ok = mbar_test(bar, par);
+    if (!ok) {
+        const long long t0 = clock64();
+        while (!(ok = mbar_test(bar, par)) && clock64() - t0 <= kWaitCycles) {
+        }
+    }
+    if (__any_sync(0xffffffffu, !ok)) {
+        if (!ok) raise_error(TC_DEVERR_WAIT);
+        st.failed = true;
+    }
+}
+
+// One warp task of G >= 4 lanes per partner, probed from the staged batches.
+// Returns this lane's hits (summed over the partner's G lanes by the caller).
+template <int MODE, bool PV>
+__device__ __forceinline__ int probe_task_staged(const Table& tb, const int32_t* __restrict__ colr, StageCtx& st,
+                                                 int G, int ppt, bool valid, int64_t qb, int dq, int x_exit) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, sub = lane / G, r = lane % G;
+    const int W = kVec * G;
+    const int nv = valid ? (dq + 3) >> 2 : 0;
+    int nb = (nv + W - 1) / W;
+    for (int o = 16; o; o >>= 1) nb = max(nb, __shfl_xor_sync(FULL, nb, o));
+    bool live = nv > 0;
+    int myc = 0;
+    const unsigned gmask = (G >= 32 ? FULL : ((1u << G) - 1u)) << (sub * G);
+    stage_issue(colr, st, G, ppt, qb, nv, live, 0);
+    for (int b = 0; b < nb; ++b) {
+        const unsigned k = st.issued - 1;  // this batch
+        if (b + 1 < nb) stage_issue(colr, st, G, ppt, qb, nv, live, b + 1);
+        stage_wait(st, k);
+        if (st.failed) break;
+        const int4* __restrict__ sv = st.buf + (size_t)(k & 1u) * kSlotVec + sub * W;
+        const int hi = nv - b * W, lo = max(0, hi - W);
+        bool stop = false;
+        if (live && hi > 0) {
+            int4 w[kVec];
+#pragma unroll
+            for (int u = 0; u < kVec; ++u) {
+                const int vv = hi - 1 - r - u * G;
+                w[u] = vv >= lo ? sv[vv - lo] : make_int4(-1, -1, -1, -1);
+            }
+#pragma unroll
+            for (int u = 0; u < kVec; ++u)
+                myc += probe1<MODE, PV>(tb, w[u].x) + probe1<MODE, PV>(tb, w[u].y) + probe1<MODE, PV>(tb, w[u].z) +
+                       probe1<MODE, PV>(tb, w[u].w);
+            const int4 t = w[kVec - 1];
+            stop = max(max(t.x, t.y), max(t.z, t.w)) < x_exit || lo == 0;
+        }
+        // a partner stops once any of its lanes saw its lowest vector below the table
+        // (or its list is used up); the next batch, already issued, is not probed
+        const unsigned sm = __ballot_sync(FULL, stop);
+        if (sm & gmask) live = false;
+        if (!__any_sync(FULL, live)) {
+            if (b + 1 < nb) stage_wait(st, k + 1);
+            break;
+        }
     }
     return myc;
 }
@@ -565,7 +734,7 @@ __device__ __forceinline__ int probe_list_padded(const Table& tb, const int32_t*
 template <bool PV, int MODE>
 __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, const int32_t* __restrict__ L,
                                                            const Table& tb, int64_t pbase, int pb, int pe, int pmax,
-                                                           const CtaScratch& sc) {
+                                                           const CtaScratch& sc, StageCtx* st) {
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
     unsigned long long acc = 0;
@@ -637,6 +806,7 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             const int x_exit = (dq >= kSortedMin && dq <= kSortedMax) ? tb.xthr : INT_MIN;
             int myc;
             if constexpr (MODE == kModeBsearch) myc = probe_list_bsearch<PV>(tb, L, qb, dq, r, G);
+            else if (st && G >= 4 && !st->failed) myc = probe_task_staged<MODE, PV>(tb, L, *st, G, ppt, valid, qb, dq, x_exit);
             else myc = probe_list_padded<MODE, PV>(tb, L, qb, dq, r, G, x_exit);
             for (int off = G >> 1; off; off >>= 1) myc += __shfl_xor_sync(FULL, myc, off);
             if (r == 0 && valid && myc) {
@@ -658,10 +828,21 @@ static int cta_table_ints(int cap, int bitmap_bits) {
 }
 
 // partners sorted per sub-chunk: kCtaPer per thread
+__host__ __device__ __forceinline__ size_t cta_smem_bytes_dev(int u_ints, int threads) {
+    const int pmax = kCtaPer * threads;
+    return (size_t)((u_ints + 1) & ~1) * sizeof(int) + (size_t)pmax * (sizeof(int64_t) + 2 * sizeof(int) + 1) +
+           (3 * kClasses + 4 + 33) * sizeof(int) + 16;
+}
 static size_t cta_smem_bytes(int u_ints, int threads) {
     const int pmax = kCtaPer * threads;
     return (size_t)((u_ints + 1) & ~1) * sizeof(int) + (size_t)pmax * (sizeof(int64_t) + 2 * sizeof(int) + 1) +
            (3 * kClasses + 4 + 33) * sizeof(int) + 16;
+}
+
+// staged kernel: two slots and two mbarriers per warp after the partner scratch
+static size_t cta_stage_offset(int u_ints, int threads) { return (cta_smem_bytes(u_ints, threads) + 127) & ~(size_t)127; }
+static size_t cta_stage_bytes(int u_ints, int threads) {
+    return cta_stage_offset(u_ints, threads) + (size_t)(threads / 32) * (2 * kSlotVec * 16 + 16);
 }
 
 __device__ __forceinline__ void block_minmax(int& mn, int& mx, int* red) {
@@ -678,12 +859,13 @@ __device__ __forceinline__ void block_minmax(int& mn, int& mx, int* red) {
     __syncthreads();
 }
 
-// BIG = false: at most 256 threads, registers capped for 5 resident CTAs per SM
-template <bool PV, int PROBE, bool BIG>
+// BIG = false: at most 256 threads, registers capped for 4 resident CTAs per SM
+// (3 with STAGED partner lists, whose slots take 32 KB more shared memory)
+template <bool PV, int PROBE, bool BIG, bool STAGED>
 #ifndef TC_CTA_MIN_BLOCKS
 #define TC_CTA_MIN_BLOCKS 4
 #endif
-__global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS) k_count_cta(CountArgs a) {
+__global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_CTA_MIN_BLOCKS)) k_count_cta(CountArgs a) {
     extern __shared__ __align__(16) int smem[];
     int* U = smem;
     CtaScratch sc;
@@ -697,6 +879,28 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
     sc.misc = sc.toff + kClasses;
     sc.scan = sc.misc + 4;
     sc.tcls = reinterpret_cast<unsigned char*>(sc.scan + 33);
+    // staged partner lists: this warp's two slots and mbarriers
+    StageCtx stage{};
+    StageCtx* st = nullptr;
+    if (STAGED) {
+        const size_t off = (cta_smem_bytes_dev(a.u_ints, blockDim.x) + 127) & ~(size_t)127;
+        char* base = reinterpret_cast<char*>(smem) + off;
+        const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        stage.buf = reinterpret_cast<int4*>(base) + (size_t)warp * 2 * kSlotVec;
+        unsigned long long* bars = reinterpret_cast<unsigned long long*>(base + (size_t)nw * 2 * kSlotVec * 16);
+        stage.bar = smem_u32(bars + 2 * warp);
+        stage.issued = 0;
+        stage.failed = false;
+        if ((threadIdx.x & 31) == 0) {
+            mbar_init(stage.bar, 1);
+            mbar_init(stage.bar + 8u, 1);
+            // the initialised barriers are visible to the copy engine (async proxy)
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncwarp();
+        st = &stage;
+    }
     __shared__ int s_red[64];
     __shared__ unsigned long long s_acc;
     // the next work item, fetched one iteration ahead by thread 0 so that the
@@ -743,6 +947,14 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
         tb.len = len;
         tb.xthr = INT_MIN;
         tb.sbase = (unsigned)__cvta_generic_to_shared(U);
+        tb.ucap = a.u_ints;
+        tb.wmax = wmax;
+        tb.llen = PROBE == kProbeHash ? a.colr_len : a.colp_len;
+        if (TC_DEBUG) {  // the table region is all zeros at the start of every item
+            bool dirty = false;
+            for (int i = threadIdx.x; i < a.u_ints; i += blockDim.x) dirty |= U[i] != 0;
+            if (dirty) raise_error(TC_DEVERR_DIRTY);
+        }
         int mode = PROBE == kProbeHash ? kModeHash : kModeBsearch;
         if (PROBE == kProbeHash && a.bitmap_bits > 0) {
             int mn, mx;
@@ -780,10 +992,16 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
         int nflush = 0;
         if (mode == kModeDirect32) {
             tb.cell32 = reinterpret_cast<unsigned*>(U);
-            for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell32[L[lb + i] - tb.lo] = kMark32;
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const unsigned off = (unsigned)(L[lb + i] - tb.lo);
+                if (dbg_ok(off < (unsigned)tb.span, TC_DEVERR_BOUNDS)) tb.cell32[off] = kMark32;
+            }
         } else if (mode == kModeDirect) {
             tb.cell = reinterpret_cast<unsigned short*>(U);
-            for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cell[L[lb + i] - tb.lo] = (unsigned short)kMark16;
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const unsigned off = (unsigned)(L[lb + i] - tb.lo);
+                if (dbg_ok(off < (unsigned)tb.span, TC_DEVERR_BOUNDS)) tb.cell[off] = (unsigned short)kMark16;
+            }
         } else if (mode == kModeBitmap) {
             const int W = (tb.span + 31) >> 5;
             unsigned* bits = reinterpret_cast<unsigned*>(U);
@@ -825,11 +1043,11 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : TC_CTA_MIN_BLOCKS)
         }
         __syncthreads();
         unsigned long long acc;
-        if (mode == kModeDirect32) acc = cta_partners<PV, kModeDirect32>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
-        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc);
+        if (mode == kModeDirect32) acc = cta_partners<PV, kModeDirect32>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
+        else if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
+        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
+        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
+        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
@@ -1000,9 +1218,11 @@ __global__ void __launch_bounds__(256) k_count_small(CountArgs a) {
         unsigned long long cu = 0;
         for (int i = 0; i < du; ++i) {
             const int v = a.colp[ub + i];
+            if (!dbg_ok(v >= 0 && v < a.n, TC_DEVERR_BOUNDS)) continue;
             const int dv = a.dp[v];
             if (dv == 0 || dv > sm) continue;
             const int64_t vb = a.rpp[v];
+            if (!dbg_ok(ub + du <= a.colp_len && vb + dv <= a.colp_len, TC_DEVERR_BOUNDS)) continue;
             int x = 0, y = 0, c = 0;
             while (x < du && y < dv) {
                 const int xa = a.colp[ub + x], yb = a.colp[vb + y];
@@ -1032,6 +1252,71 @@ __global__ void __launch_bounds__(256) k_count_small(CountArgs a) {
         __syncthreads();
         if (threadIdx.x == 0 && s_acc) atomicAdd(&a.totals[0], s_acc);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Merge-path class: one warp per oriented edge (u, v) with balanced lists
+// (the paper's TwoLarge intersection, Sec. 4.2.2, with the merge path split
+// evenly over the 32 lanes).  Both lists are N+ rows of the oriented CSR in
+// ascending vertex id.  Lane l takes diagonals [l L/32, (l+1) L/32) of the
+// merge path of length L = |N+(u)| + |N+(v)|, finds its start by binary search
+// (A = N+(u) is taken first on ties, so a common w is counted when its copy in
+// A is consumed, by exactly one lane) and walks its diagonals.
+// ---------------------------------------------------------------------------
+template <bool PV>
+__global__ void __launch_bounds__(256) k_count_merge(CountArgs a, const int2* __restrict__ medge,
+                                                     const unsigned long long* __restrict__ n_medge,
+                                                     unsigned long long cap) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long n_all = min(*n_medge, cap);
+    const unsigned long long e_lo = n_all * a.shard / a.nshards, e_hi = n_all * (a.shard + 1) / a.nshards;
+    const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc = 0;
+    for (unsigned long long e = e_lo + warp; e < e_hi; e += nwarps) {
+        const int2 uv = medge[e];
+        if (!dbg_ok(uv.x >= 0 && uv.x < a.n && uv.y >= 0 && uv.y < a.n, TC_DEVERR_BOUNDS)) continue;
+        const int64_t ab = a.rpp[uv.x], bb = a.rpp[uv.y];
+        const int na = (int)(a.rpp[uv.x + 1] - ab), nb = (int)(a.rpp[uv.y + 1] - bb);
+        if (!dbg_ok(ab + na <= a.colp_len && bb + nb <= a.colp_len, TC_DEVERR_BOUNDS)) continue;
+        const int32_t* __restrict__ A = a.colp + ab;
+        const int32_t* __restrict__ Bv = a.colp + bb;
+        const int L = na + nb;
+        const int d0 = (int)(((long long)L * lane) >> 5), d1 = (int)(((long long)L * (lane + 1)) >> 5);
+        // i = number of A elements among the first d0 merged ones
+        int lo = max(0, d0 - nb), hi = min(d0, na);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= Bv[d0 - mid - 1]) lo = mid + 1;
+            else hi = mid;
+        }
+        int i = lo, j = d0 - lo, c = 0;
+        for (int step = d0; step < d1; ++step) {
+            const int x = i < na ? A[i] : INT_MAX;
+            const int y = j < nb ? Bv[j] : INT_MAX;
+            if (x <= y) {
+                if (x == y) {
+                    ++c;
+                    if (PV) atomicAdd(&a.t[x], 1ull);
+                }
+                ++i;
+            } else {
+                ++j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        if (lane == 0 && c) {
+            if (PV) {
+                atomicAdd(&a.t[uv.x], (unsigned long long)c);
+                atomicAdd(&a.t[uv.y], (unsigned long long)c);
+            }
+            if (a.row_graph) atomicAdd(&a.totals[a.row_graph[uv.x]], (unsigned long long)c);
+            else acc += (unsigned long long)c;
+        }
+    }
+    if (!a.row_graph && lane == 0 && acc) atomicAdd(&a.totals[0], acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1075,8 +1360,10 @@ static cudaError_t launch_tables(tc_ctx* ctx, const CountArgs& base, const tc_oc
         a.items_cap = (unsigned long long)o->items_cta_cap;
         a.queue = queues + 1;
         a.u_ints = cta_table_ints(a.cap, a.bitmap_bits);
-        const size_t smem = cta_smem_bytes(a.u_ints, tun.cta_threads);
-        auto kern = tun.cta_threads <= 256 ? k_count_cta<PV, PROBE, false> : k_count_cta<PV, PROBE, true>;
+        const bool staged = PROBE == kProbeHash && tun.stage > 0 && tun.cta_threads <= 256;
+        const size_t smem = staged ? cta_stage_bytes(a.u_ints, tun.cta_threads) : cta_smem_bytes(a.u_ints, tun.cta_threads);
+        auto kern = staged ? k_count_cta<PV, PROBE, false, true>
+                           : (tun.cta_threads <= 256 ? k_count_cta<PV, PROBE, false, false> : k_count_cta<PV, PROBE, true, false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tun.cta_threads, smem);
@@ -1118,6 +1405,8 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.shard = shard;
     a.nshards = nshards;
     a.colr = o->colr;
+    a.colr_len = std::max<int64_t>(o->m, 1) + 3 * o->n + 4;
+    a.colp_len = std::max<int64_t>(o->m, 1) + 4;
     a.perm = o->perm;
     a.rspan = o->rspan;
     a.bitmap_bits = tun.bitmap_bits;
@@ -1134,6 +1423,20 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
         } else {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_small<false>, 256, 0);
             k_count_small<false><<<(unsigned)(ns * std::max(per_sm, 1)), 256, 0, s>>>(a);
+        }
+    }
+    if (o->medge) {
+        PhaseScope ph(ctx, kPhCountMerge, s);
+        TC_LAUNCH(ctx);
+        int per_sm = 0;
+        if (per_vertex) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_merge<true>, 256, 0);
+            k_count_merge<true><<<(unsigned)(ns * std::max(per_sm, 1)), 256, 0, s>>>(a, o->medge, &o->dc->n_merge_edges,
+                                                                                     (unsigned long long)o->medge_cap);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_merge<false>, 256, 0);
+            k_count_merge<false><<<(unsigned)(ns * std::max(per_sm, 1)), 256, 0, s>>>(a, o->medge, &o->dc->n_merge_edges,
+                                                                                      (unsigned long long)o->medge_cap);
         }
     }
     if (tun.probe == kProbeBsearch) {

@@ -19,6 +19,7 @@ struct DevCounters {
     unsigned long long n_items_cta;    // work items of the CTA-table class
     unsigned long long n_pivot_edges;  // oriented edges assigned to a pivot
     unsigned long long n_small_edges;  // oriented edges merged thread-per-edge
+    unsigned long long n_merge_edges;  // oriented edges of the warp merge-path class
     int error;                         // validation verdict (0 = ok)
     int max_dplus;                     // max out-degree after orientation
     int max_deg;                       // max degree of the input
@@ -40,6 +41,9 @@ struct Tuning {
     int chunk = 512;
     int bitmap_bits = 131072;  // CTA items whose list spans <= this many rank ids use a bitmap
     int direct_span = 16384;   // ... and <= this many a direct 16-bit cell per rank id
+    int merge_ratio = 0;       // percent; balanced edges (max/min d+ <= ratio, max <= merge_max) merge; 0 = off
+    int merge_max = 256;
+    int stage = 0;             // CTA kernel: 1 = lists of >= 4 lanes per partner staged by the copy engine; 0 = per-lane loads
 };
 
 }  // namespace tc
@@ -92,6 +96,8 @@ struct tc_ocsr {
     tc::Item* items_warp = nullptr;
     tc::Item* items_cta = nullptr;
     int64_t items_warp_cap = 0, items_cta_cap = 0;
+    int2* medge = nullptr;      // oriented edges (u, v) of the merge-path class (first n_merge_edges used)
+    int64_t medge_cap = 0;
     tc::DevCounters* dc = nullptr;
     // batch mode: vertex -> graph id and the number of graphs
     int32_t* row_graph = nullptr;
@@ -119,7 +125,7 @@ namespace tc {
 enum Phase {
     kPhDegree = 0, kPhValidate, kPhOrientCount, kPhOrientScan, kPhOrientScatter, kPhPivotCount, kPhPivotScan,
     kPhPivotScatter, kPhItems, kPhCountSmall, kPhCountWarp, kPhCountCta, kPhEdgeSort, kPhCountInit, kPhRank,
-    kPhRowSort, kNumPhases
+    kPhRowSort, kPhCountMerge, kNumPhases
 };
 
 // RAII phase marker: records an event pair on `s` when tracing is on.

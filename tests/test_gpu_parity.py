@@ -127,6 +127,17 @@ CONFIGS = [
     dict(direct_span=-1, bitmap_bits=64, warp_max=4),
     dict(direct_span=40, warp_max=4, chunk=9),
     dict(bitmap_bits=262144, table_cap=64, warp_max=8, chunk=5),
+    # the CTA-table kernel with partner lists staged by the copy engine, over
+    # every table kind, small tables and tiny work items
+    dict(stage=1),
+    dict(stage=1, table_cap=64, warp_max=8, chunk=5),
+    dict(stage=1, table_cap=16, warp_max=2, chunk=1),
+    dict(stage=1, direct_span=-1, bitmap_bits=-1),
+    # the degree-ratio switch: balanced edges take the warp merge path
+    dict(merge_ratio=200),
+    dict(merge_ratio=100, merge_max=16),
+    dict(merge_ratio=1000000, merge_max=4096),
+    dict(merge_ratio=400, small_max=-1, warp_max=8),
 ]
 
 
@@ -136,6 +147,19 @@ def test_partition_configs(B, cfg):
     for g in (gen.rmat(13, 16, seed=7), gen.ba(3000, 12, seed=1), gen.grid(40, 40, seed=0), gen.er(1024, 8192, seed=9)):
         assert_parity(c, g)
         assert_parity(c, g, per_vertex=False)
+    c.close()
+
+
+def test_merge_class_takes_the_balanced_edges(B):
+    """With every non-small edge below the ratio bound, the whole count runs on
+    the merge path (and the tables get no work), still bit-exact."""
+    g = gen.er(4096, 65536, seed=3)   # d+ mostly 10..30: balanced lists
+    c = B.Context(0, merge_ratio=1000000, merge_max=4096)
+    c.set_trace(True)
+    assert_parity(c, g)
+    tr = c.read_trace()
+    assert tr["phase_calls"]["count_merge"] >= 1
+    c.close()
 
 
 # ---------------------------------------------------------------- closed forms, edge cases
