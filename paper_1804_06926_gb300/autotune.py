@@ -11,7 +11,10 @@ speed; the tuner checks that every candidate returns the same total.
 Knobs: the probe strategy (hash/bitmap/direct tables or binary search), the
 thread-per-edge and warp-table thresholds (small_max, warp_max), the CTA
 table capacity (table_cap), partners per work item (chunk), threads per CTA
-(cta_threads) and the bitmap/direct span limits.
+(cta_threads), the bitmap/direct span limits, the degree-ratio switch that
+sends balanced edges to the warp merge path (merge_ratio, merge_max; the
+paper's choice between its two intersection strategies, Sec. 4.2.2), and the
+staging of partner lists by the copy engine (stage).
 """
 from __future__ import annotations
 
@@ -33,6 +36,9 @@ CANDIDATES = [
     {"table_cap": 2048, "chunk": 2048},
     {"direct_span": -1},
     {"probe": 2},
+    {"merge_ratio": 150, "merge_max": 128},
+    {"merge_ratio": 300, "merge_max": 512},
+    {"stage": 1},
 ]
 
 

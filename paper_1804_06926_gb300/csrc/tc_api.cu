@@ -168,7 +168,7 @@ static tc_status count_any(tc_ctx* ctx, const tc_ocsr* o, int64_t* totals, int64
 static void release_ocsr(tc_ocsr* o, cudaStream_t s, bool async) {
     if (!o) return;
     void* ptrs[] = {o->rpp,  o->colp, o->dplus,      o->deg, o->rank,      o->perm, o->colr,     o->rspan,
-                    o->prp, o->pcol, o->items_warp, o->items_cta, o->dc,   o->row_graph, o->medge};
+                    o->prp, o->pcol, o->items_warp, o->items_cta, o->dc,   o->row_graph, o->medge, o->pdesc};
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(o->device);

@@ -210,7 +210,12 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ r
 #define TC_CTA_CHUNK_MUL 2
 #endif
 constexpr int kMpThreads = 256;
-constexpr int kMpIpt = 8;
+#ifndef TC_MP_IPT
+#define TC_MP_IPT 8
+#endif
+constexpr int kMpIpt = TC_MP_IPT;   // items per thread of a tile (a multiple of 8)
+static_assert(kMpIpt % 8 == 0, "tile rows are handled as 16-byte vectors of 8 entries");
+constexpr int kRowVec = kMpIpt / 8;
 constexpr int kMpTile = kMpThreads * kMpIpt;
 // resident CTAs per SM the tile kernels are compiled for (registers permitting):
 // they wait on scattered loads, so more warps in flight hide more latency
@@ -267,7 +272,8 @@ __device__ void mp_tile(MpTile<BATCH>& S, int64_t t, int64_t n, const longlong2*
             if (BATCH) S.base[k] = (int)vtx_off[row_graph[i0 + k]];
         }
     }
-    reinterpret_cast<uint4*>(S.row)[threadIdx.x] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int c = 0; c < kRowVec; ++c) reinterpret_cast<uint4*>(S.row)[threadIdx.x * kRowVec + c] = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) {
         S.i0 = i0;
         S.j0 = j0;
@@ -282,8 +288,10 @@ __device__ void mp_tile(MpTile<BATCH>& S, int64_t t, int64_t n, const longlong2*
     for (int k = 1 + threadIdx.x; k < nr; k += blockDim.x)
         if (S.cs[k] < S.cs[k + 1]) S.row[S.cs[k]] = (unsigned short)k;
     __syncthreads();
-    uint4 pk = reinterpret_cast<uint4*>(S.row)[threadIdx.x];
-    unsigned short* v = reinterpret_cast<unsigned short*>(&pk);
+    uint4 pk[kRowVec];
+#pragma unroll
+    for (int c = 0; c < kRowVec; ++c) pk[c] = reinterpret_cast<uint4*>(S.row)[threadIdx.x * kRowVec + c];
+    unsigned short* v = reinterpret_cast<unsigned short*>(pk);
     int run = 0;
 #pragma unroll
     for (int q = 0; q < kMpIpt; ++q) {
@@ -304,7 +312,8 @@ __device__ void mp_tile(MpTile<BATCH>& S, int64_t t, int64_t n, const longlong2*
     for (int k = 0; k < w; ++k) before = max(before, S.wmax[k]);
 #pragma unroll
     for (int q = 0; q < kMpIpt; ++q) v[q] = (unsigned short)max(before, (int)v[q]);
-    reinterpret_cast<uint4*>(S.row)[threadIdx.x] = pk;
+#pragma unroll
+    for (int c = 0; c < kRowVec; ++c) reinterpret_cast<uint4*>(S.row)[threadIdx.x * kRowVec + c] = pk[c];
     __syncthreads();
 }
 
@@ -393,10 +402,12 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(i
 
 // rpp[u] = kept entries before row u, and d+(u) (and its maximum)
 // (and (rank(u), d+(u)) packed, so that the scatter gathers both of a
-// neighbour with one 8-byte load)
+// neighbour with one 8-byte load, and (first vector of u's colr row, d+(u)),
+// the descriptor the count kernels read for a partner u)
 __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned* __restrict__ keep,
                        const int64_t* __restrict__ kpre, const int32_t* __restrict__ rank, int64_t* __restrict__ rpp,
-                       int32_t* __restrict__ dplus, int2* __restrict__ rd2, int* __restrict__ max_dplus) {
+                       int32_t* __restrict__ dplus, int2* __restrict__ rd2, int2* __restrict__ pd2,
+                       int* __restrict__ max_dplus) {
     int mx = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = bits_before(keep, kpre, rp[u]);
@@ -405,6 +416,7 @@ __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned
             const int d = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
             dplus[u] = d;
             rd2[u] = make_int2(rank[u], d);
+            pd2[u] = make_int2((int)((s + 3 * u + 3) >> 2), d);  // colr_row(rpp, u) / 4
             mx = max(mx, d);
         }
     }
@@ -716,6 +728,16 @@ __global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_sc
     }
 }
 
+// pdesc[i] = (first vector of pcol[i]'s colr row, its d+) for every partner
+// entry: what the count kernels read per partner, stored beside pcol so that
+// they load it with pcol instead of gathering it through the partner's id.
+__global__ void k_pdesc(const unsigned long long* __restrict__ n_pivot, const int32_t* __restrict__ pcol,
+                        const int2* __restrict__ pd2, int2* __restrict__ pdesc) {
+    const int64_t np = (int64_t)*n_pivot;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x)
+        pdesc[i] = pd2[pcol[i]];
+}
+
 // Work items per pivot, pivots taken in descending rank order.  Warp class
 // (d+(p) <= warp_max): one item per chunk of partners.  CTA class: one item per
 // (segment of the pivot list, chunk_c partners); a segment holds at most
@@ -784,6 +806,9 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     const Tuning tun = ctx->tun;
     const bool batch = vtx_off != nullptr;
     const int64_t m = nnz / 2;
+    // partner descriptors hold colr vector indexes as int32
+    if ((m + 3 * n + 4) / 4 > (int64_t)0x7fffffff)
+        return set_err(ctx, TC_ERR_INVALID_ARG, "graph too large: m + 3n must stay below 2^33");
     tc_ocsr* o = new tc_ocsr();
     o->device = ctx->device;
     o->n = n;
@@ -823,6 +848,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     A((void**)&o->rspan, sizeof(int2) * std::max<int64_t>(n, 1));
     A((void**)&o->prp, sizeof(int64_t) * n1);
     A((void**)&o->pcol, sizeof(int32_t) * std::max<int64_t>(m, 1));
+    A((void**)&o->pdesc, sizeof(int2) * std::max<int64_t>(m, 1));
     A((void**)&o->items_warp, sizeof(Item) * o->items_warp_cap);
     A((void**)&o->items_cta, sizeof(Item) * o->items_cta_cap);
     A((void**)&o->dc, sizeof(DevCounters));
@@ -839,7 +865,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         return set_err(ctx, TC_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
     deg = o->deg;
-    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (3 * m + 9 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
+    o->bytes = (int64_t)(sizeof(int64_t) * n1 * 2 + sizeof(int32_t) * (5 * m + 9 * n) + sizeof(Item) * (o->items_warp_cap + o->items_cta_cap)
                          + (batch ? sizeof(int32_t) * n : 0) + sizeof(int2) * o->medge_cap);
     cudaMemsetAsync(o->dc, 0, sizeof(DevCounters), s);
 
@@ -903,6 +929,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     int32_t* wpc = nullptr;
     int64_t *kpre = nullptr, *upre = nullptr, *vpre = nullptr;
     int2* rd2 = nullptr;
+    int2* pd2 = nullptr;
     unsigned long long* vtop = nullptr;
     void* wtmp = nullptr;
     const size_t wtb = scan_tmp_bytes(std::max(kw, std::max(uw, n)));
@@ -918,12 +945,13 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     B((void**)&upre, sizeof(int64_t) * (uw + 1));
     B((void**)&vpre, sizeof(int64_t) * n1);
     B((void**)&rd2, sizeof(int2) * std::max<int64_t>(n, 1));
+    B((void**)&pd2, sizeof(int2) * std::max<int64_t>(n, 1));
     B((void**)&vtop, sizeof(unsigned long long) * std::max<int64_t>(n, 1));
     B(&wtmp, wtb);
     auto free_tmp = [&]() {
         dev_free(coord, s); dev_free(keep, s); dev_free(umask, s); dev_free(vmask, s); dev_free(wpc, s);
         dev_free(kpre, s); dev_free(upre, s); dev_free(vpre, s); dev_free(wtmp, s);
-        dev_free(rd2, s); dev_free(vtop, s);
+        dev_free(rd2, s); dev_free(pd2, s); dev_free(vtop, s);
         dev_free(pc, s);
     };
     if (e != cudaSuccess) {
@@ -951,7 +979,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         k_popc<<<grid_for(kw, 256, ns), 256, 0, s>>>(keep, kw, wpc);
         scan_i32_to_i64(wpc, kpre, kw, wtmp, wtb, s);
         // row offsets and d+
-        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rank, o->rpp, o->dplus, rd2,
+        k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rank, o->rpp, o->dplus, rd2, pd2,
                                                         &o->dc->max_dplus);
         ctx->launches += 5;
     }
@@ -1006,11 +1034,14 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         if (nt2 > 0) {
             k_pivot_scatter<<<g2, kMpThreads, 0, s>>>(n, nt2, coord, o->rpp, o->colp, umask, vmask, upre, vpre, vtop, o->pcol);
             TC_LAUNCH(ctx);
+            // the partners' descriptors beside pcol, in one coalesced pass
+            k_pdesc<<<grid_for(m, 256, ns), 256, 0, s>>>(&o->dc->n_pivot_edges, o->pcol, pd2, o->pdesc);
+            TC_LAUNCH(ctx);
         }
     }
     dev_free(coord, s); dev_free(keep, s); dev_free(umask, s); dev_free(vmask, s); dev_free(wpc, s);
     dev_free(kpre, s); dev_free(upre, s); dev_free(vpre, s); dev_free(wtmp, s);
-    dev_free(rd2, s); dev_free(vtop, s);
+    dev_free(rd2, s); dev_free(pd2, s); dev_free(vtop, s);
     if (n > 0) {
         PhaseScope ph(ctx, kPhItems, s);
         k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->perm, o->dplus, o->prp, tun.warp_max, tun.table_cap, tun.chunk,

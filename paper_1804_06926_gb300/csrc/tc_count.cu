@@ -40,6 +40,7 @@ struct CountArgs {
     const int32_t* dp;
     const int64_t* prp;
     const int32_t* pcol;
+    const int2* pdesc;            // beside pcol: (first vector of the partner's colr row, its d+)
     const Item* items;
     const unsigned long long* n_items;
     unsigned long long items_cap;   // allocated items (n_items never exceeds it; clamped anyway)
@@ -382,8 +383,9 @@ __device__ __forceinline__ unsigned long long warp_partners_vec(const CountArgs&
     int64_t qvn = 0;
     if (pb + lane < pe) {
         qn = a.pcol[pbase + pb + lane];
-        qvn = colr_row(a.rpp, qn) >> 2;
-        nvn = (a.dp[qn] + 3) >> 2;
+        const int2 d = a.pdesc[pbase + pb + lane];
+        qvn = d.x;
+        nvn = (d.y + 3) >> 2;
     }
     for (int g0 = pb; g0 < pe; g0 += 32) {
         const bool valid = g0 + lane < pe;
@@ -392,8 +394,9 @@ __device__ __forceinline__ unsigned long long warp_partners_vec(const CountArgs&
         const int nvq = nvn;     // >= 1: partner lists are non-empty
         if (g0 + 32 + lane < pe) {
             qn = a.pcol[pbase + g0 + 32 + lane];
-            qvn = colr_row(a.rpp, qn) >> 2;
-            nvn = (a.dp[qn] + 3) >> 2;
+            const int2 d = a.pdesc[pbase + g0 + 32 + lane];
+            qvn = d.x;
+            nvn = (d.y + 3) >> 2;
         } else {  // past the last partner: an empty descriptor
             qn = 0;
             qvn = 0;
@@ -754,8 +757,14 @@ __device__ __forceinline__ unsigned long long cta_partners(const CountArgs& a, c
             rb[k] = 0;
             if (i < NP) {
                 rq[k] = a.pcol[pbase + c0 + i];
-                rb[k] = MODE == kModeBsearch ? a.rpp[rq[k]] : colr_row(a.rpp, rq[k]);
-                rd[k] = a.dp[rq[k]];
+                if (MODE == kModeBsearch) {
+                    rb[k] = a.rpp[rq[k]];
+                    rd[k] = a.dp[rq[k]];
+                } else {  // the descriptor the build stored beside the partner
+                    const int2 d = a.pdesc[pbase + c0 + i];
+                    rb[k] = (int64_t)d.x << 2;
+                    rd[k] = d.y;
+                }
                 rc[k] = min(kClasses - 1, 31 - __clz(rd[k]));
                 rs[k] = atomicAdd(&sc.ccnt[rc[k]], 1);
             }
@@ -1396,6 +1405,7 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.dp = o->dplus;
     a.prp = o->prp;
     a.pcol = o->pcol;
+    a.pdesc = o->pdesc;
     a.totals = totals;
     a.t = per_vertex;
     a.row_graph = o->row_graph;

@@ -93,6 +93,7 @@ struct tc_ocsr {
     int2* rspan = nullptr;      // [n] smallest and largest rank id of each row with d+ > warp_max (others unset)
     int64_t* prp = nullptr;     // [n+1] partner row offsets
     int32_t* pcol = nullptr;    // [m] partners (only the first n_pivot_edges used)
+    int2* pdesc = nullptr;      // [m] beside pcol: (first 16-byte vector of the partner's colr row, its d+)
     tc::Item* items_warp = nullptr;
     tc::Item* items_cta = nullptr;
     int64_t items_warp_cap = 0, items_cta_cap = 0;

@@ -103,7 +103,7 @@ int64_t estimate_bytes(int64_t n, int64_t nnz, const tc::Tuning& t) {
     const int64_t dmax = std::max<int64_t>(1, (int64_t)std::sqrt((double)(2 * m)) + 1);
     const int64_t iw = std::min(n, m) + m / t.chunk + 2;
     const int64_t ic = dmax * m / ((int64_t)t.table_cap * t.chunk) + m / t.table_cap + m / t.chunk + m / (t.warp_max + 1) + 6;
-    const int64_t ocsr = 16 * (n + 1) + 4 * (3 * m + 9 * n) + 16 * (iw + ic) + (t.merge_ratio > 0 ? 8 * m : 0);
+    const int64_t ocsr = 16 * (n + 1) + 4 * (5 * m + 9 * n) + 16 * (iw + ic) + (t.merge_ratio > 0 ? 8 * m : 0);
     const int64_t input = 8 * (n + 1) + 4 * nnz;
     const int64_t scratch = 8 * n + 64 * 1024 + 8 * (n + 1);  // deg, pc, scan tiles, outputs
     return ocsr + input + scratch + (1 << 20);
