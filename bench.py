@@ -748,11 +748,34 @@ def run_secondary(args, torch, binding, dev):
     many = serve_saturated(binding, dev, graphs, ids, args.slots, 0)
     one = serve_saturated(binding, dev, graphs, ids, 1, 1)
     assert many[3] == one[3], "served totals differ between the mixed and the one-at-a-time server"
+    # latency: an open-loop Poisson stream at 0.7x the saturated request rate
+    rate = 0.7 * many[1]
+    nreq = 1000
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    picks = rng.integers(0, len(graphs), nreq)
+    srv = binding.Server(device=dev.index, slots=args.slots, hbm_budget_bytes=40 << 30)
+    tickets, lat = [], []
+    start = time.perf_counter()
+    for i in range(nreq):
+        now = time.perf_counter() - start
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        g = graphs[int(picks[i])]
+        tickets.append(srv.submit(g.n, g.row_ptr, g.col, key=int(picks[i]) + 1))
+    for tk in tickets:
+        r = srv.wait(tk, 600000)
+        assert r["status"] == 0
+        lat.append(r["latency_ms"])
+        srv.release(tk)
+    srv.close()
     out["serving_saturated"] = {
         "requests": len(ids), "clients": 8, "pool": "32 graphs: R-MAT s10-16 ef16 and BA n~U[100,20000], k~U[2,16]",
         "slots": args.slots, "edges_per_s": many[0], "requests_per_s": many[1], "fused_batches": many[2],
         "one_slot_edges_per_s": one[0], "one_slot_requests_per_s": one[1], "gain": many[0] / one[0],
         "totals_equal_alone_and_mixed": True}
+    lat = np.array(lat)
+    out["serving_poisson"] = {"requests": nreq, "rate_per_s": rate, "slots": args.slots, "resident_cache": True,
+                              "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
     return out
 
 

@@ -47,6 +47,7 @@ struct CountArgs {
     unsigned int* queue;
     unsigned long long* totals;   // [G] (batch) or [1]
     unsigned long long* t;        // per-vertex counts or nullptr
+    unsigned long long* t_rank;   // with t: counts of table keys, indexed by rank id (added into t at the end)
     const int32_t* row_graph;     // batch: graph of each vertex, else nullptr
     const int32_t* colr;          // oriented lists in rank ids, row u at colr_row(rpp, u), padded with -1
     const int32_t* perm;          // rank id -> vertex id
@@ -1067,7 +1068,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
                     const int x = L[lb + i];
                     const unsigned c = mode == kModeDirect32 ? tb.cell32[x - tb.lo] & ~kMark32
                                                              : (unsigned)tb.cell[x - tb.lo] & ~kMark16;
-                    if (c) atomicAdd(&a.t[a.perm[x]], (unsigned long long)c);
+                    if (c) atomicAdd(&a.t_rank[x], (unsigned long long)c);
                 }
                 __syncthreads();
                 // clear the whole span (junk counts of non-keys included)
@@ -1087,7 +1088,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
                     const unsigned word = tb.bits[off >> 5];
                     const int ord = (int)tb.pre[off >> 5] + __popc(word & ((1u << (off & 31u)) - 1u));
                     const int c = tb.cnts[ord];
-                    if (c) atomicAdd(&a.t[a.perm[x]], (unsigned long long)c);
+                    if (c) atomicAdd(&a.t_rank[x], (unsigned long long)c);
                 }
                 __syncthreads();
                 for (int i = threadIdx.x; i < len; i += blockDim.x) tb.cnts[i] = 0;
@@ -1102,7 +1103,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
                     const int c = tb.cnts[i];
                     if (c) {
                         const int x = mode == kModeHash ? tb.keys[i] - 1 : tb.keys[i];
-                        atomicAdd(&a.t[PROBE == kProbeHash ? a.perm[x] : x], (unsigned long long)c);
+                        if (PROBE == kProbeHash) atomicAdd(&a.t_rank[x], (unsigned long long)c);
+                        else atomicAdd(&a.t[x], (unsigned long long)c);
                         tb.cnts[i] = 0;
                     }
                 }
@@ -1166,7 +1168,7 @@ __global__ void __launch_bounds__(256, TC_WARP_MIN_BLOCKS) k_count_warp(CountArg
             if (PV) {
                 for (int i = lane; i < S; i += 32) {
                     const int c = cnts[i];
-                    if (c) atomicAdd(&a.t[a.perm[keys[i] - 1]], (unsigned long long)c);
+                    if (c) atomicAdd(&a.t_rank[keys[i] - 1], (unsigned long long)c);
                 }
             }
             acc = warp_sum_u64(acc);
@@ -1328,6 +1330,17 @@ __global__ void __launch_bounds__(256) k_count_merge(CountArgs a, const int2* __
     if (!a.row_graph && lane == 0 && acc) atomicAdd(&a.totals[0], acc);
 }
 
+// The table keys' counts were accumulated by rank id (a pivot segment's keys
+// are rank ids of a short span, so those atomics share cache lines and need no
+// rank -> vertex lookup); t[perm[r]] += t_rank[r] folds them into t.
+__global__ void k_fold_rank_counts(int64_t n, const int32_t* __restrict__ perm,
+                                   const unsigned long long* __restrict__ t_rank, unsigned long long* __restrict__ t) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long c = t_rank[r];
+        if (c) t[perm[r]] += c;  // perm is a bijection: one writer per vertex
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host launch
 // ---------------------------------------------------------------------------
@@ -1386,6 +1399,7 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     const Tuning& tun = o->tun;
     const int64_t G = o->G > 0 ? o->G : 1;
     unsigned* queues = nullptr;
+    unsigned long long* t_rank = nullptr;
     {
         PhaseScope ph(ctx, kPhCountInit, s);
         cudaError_t e = cudaMemsetAsync(totals, 0, sizeof(unsigned long long) * G, s);
@@ -1396,6 +1410,14 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
         e = dev_alloc((void**)&queues, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return set_err(ctx, TC_ERR_OOM, "count: queue allocation failed");
         cudaMemsetAsync(queues, 0, 2 * sizeof(unsigned), s);
+        if (per_vertex) {
+            e = dev_alloc((void**)&t_rank, sizeof(unsigned long long) * (size_t)o->n, s);
+            if (e != cudaSuccess) {
+                dev_free(queues, s);
+                return set_err(ctx, TC_ERR_OOM, "count: rank-count allocation failed");
+            }
+            cudaMemsetAsync(t_rank, 0, sizeof(unsigned long long) * (size_t)o->n, s);
+        }
     }
     cudaError_t e = cudaSuccess;
 
@@ -1408,6 +1430,7 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
     a.pdesc = o->pdesc;
     a.totals = totals;
     a.t = per_vertex;
+    a.t_rank = t_rank;
     a.row_graph = o->row_graph;
     a.n = o->n;
     a.cap = tun.table_cap;
@@ -1456,6 +1479,14 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
         e = per_vertex ? launch_tables<true, kProbeHash>(ctx, a, o, queues, ns, tun, s)
                        : launch_tables<false, kProbeHash>(ctx, a, o, queues, ns, tun, s);
     }
+    if (e == cudaSuccess && t_rank) {
+        PhaseScope ph(ctx, kPhCountInit, s);
+        TC_LAUNCH(ctx);
+        k_fold_rank_counts<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((o->n + 255) / 256, (int64_t)ns * 8)), 256, 0,
+                             s>>>(o->n, o->perm, t_rank, per_vertex);
+        e = cudaGetLastError();
+    }
+    dev_free(t_rank, s);
     dev_free(queues, s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "count kernels");
     return TC_OK;
