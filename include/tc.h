@@ -109,7 +109,10 @@ typedef struct tc_config {
                               staged into shared memory by the copy engine (cp.async.bulk), one batch
                               ahead of the probing; 0 (default) or -1 = every lane loads its own
                               vectors (faster on GB300: the small copies wait longer than the loads) */
-    int32_t reserved[5];
+    int32_t small_lanes;   /* threads per source row of the thread-merge class (threads per edge of
+                              Sec. 4.2.2's TwoSmall): lane j of a row's group takes its edges j, j+L, ...;
+                              1, 2, 4, 8, 16 or 32; default 1 */
+    int32_t reserved[4];
 } tc_config;
 
 typedef struct tc_ctx tc_ctx;

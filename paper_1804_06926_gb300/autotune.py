@@ -9,12 +9,18 @@ with CUDA events on the launching stream, and the fastest is cached per
 speed; the tuner checks that every candidate returns the same total.
 
 Knobs: the probe strategy (hash/bitmap/direct tables or binary search), the
-thread-per-edge and warp-table thresholds (small_max, warp_max), the CTA
-table capacity (table_cap), partners per work item (chunk), threads per CTA
-(cta_threads), the bitmap/direct span limits, the degree-ratio switch that
-sends balanced edges to the warp merge path (merge_ratio, merge_max; the
-paper's choice between its two intersection strategies, Sec. 4.2.2), and the
-staging of partner lists by the copy engine (stage).
+thread-per-edge and warp-table thresholds (small_max, warp_max), threads per
+row of the thread-merge class (small_lanes), the CTA table capacity
+(table_cap), partners per work item (chunk), threads per CTA (cta_threads),
+the bitmap/direct span limits, the degree-ratio switch that sends balanced
+edges to the warp merge path (merge_ratio, merge_max; the paper's choice
+between its two intersection strategies, Sec. 4.2.2), and the staging of
+partner lists by the copy engine (stage).
+
+The search has two stages: every candidate below (one knob changed from the
+default, or a pair that only makes sense together) is measured; then, from
+the fastest, the other candidates that beat the default are merged in one at
+a time, greedily, each kept only if the merged configuration is faster.
 """
 from __future__ import annotations
 
@@ -32,6 +38,7 @@ CANDIDATES = [
     {"warp_max": 128, "chunk": 2048},
     {"small_max": 4},
     {"small_max": 16},
+    {"small_max": 32},
     {"cta_threads": 512},
     {"table_cap": 2048, "chunk": 2048},
     {"direct_span": -1},
@@ -39,6 +46,8 @@ CANDIDATES = [
     {"merge_ratio": 150, "merge_max": 128},
     {"merge_ratio": 300, "merge_max": 512},
     {"stage": 1},
+    {"small_lanes": 2},
+    {"small_lanes": 4},
 ]
 
 
@@ -102,25 +111,43 @@ class Autotuner:
             self._cache[self.key(cls)] = {"best": best, "times_ms": times}
             self._write()
 
-    def tune(self, cls: str, run, candidates=None, reps: int = 3, force: bool = False) -> TuneResult:
+    def tune(self, cls: str, run, candidates=None, reps: int = 3, force: bool = False,
+             combine: bool = True) -> TuneResult:
         """run(config) -> (milliseconds, total); the fastest config wins.
 
-        Cached classes are not re-measured unless force=True."""
+        With combine, the candidates that beat the default ({} when it is
+        among them, else the first) are merged into the fastest one greedily
+        (disjoint knobs only), each merge kept if it is faster.  Cached
+        classes are not re-measured unless force=True."""
         if not force:
             hit = self.lookup(cls)
             if hit is not None:
                 return TuneResult(self.key(cls), hit, [])
         cands = candidates if candidates is not None else CANDIDATES
-        times, ref_total, best, best_ms = [], None, None, math.inf
-        for cfg in cands:
+        times = []
+        ref = []
+
+        def measure(cfg):
             ms, total = min((run(cfg) for _ in range(max(1, reps))), key=lambda x: x[0])
-            if ref_total is None:
-                ref_total = total
-            elif total != ref_total:
-                raise RuntimeError(f"candidate {cfg} changed the count: {total} != {ref_total}")
-            times.append([cfg, ms])
-            if ms < best_ms:
-                best, best_ms = dict(cfg), ms
+            if not ref:
+                ref.append(total)
+            elif total != ref[0]:
+                raise RuntimeError(f"candidate {cfg} changed the count: {total} != {ref[0]}")
+            times.append([dict(cfg), ms])
+            return ms
+
+        measured = [(measure(cfg), dict(cfg)) for cfg in cands]
+        best_ms, best = min(measured, key=lambda x: x[0]) if measured else (math.inf, None)
+        if combine and measured:
+            base_ms = next((ms for ms, cfg in measured if not cfg), measured[0][0])
+            better = sorted((x for x in measured if x[0] < base_ms and x[1] and x[1] != best), key=lambda x: x[0])
+            for _, cfg in better:
+                if set(cfg) & set(best):
+                    continue
+                merged = {**best, **cfg}
+                ms = measure(merged)
+                if ms < best_ms:
+                    best, best_ms = merged, ms
         self.record(cls, best, times)
         return TuneResult(self.key(cls), best, times)
 

@@ -40,7 +40,8 @@ class tc_config(C.Structure):
     _fields_ = [("small_max", C.c_int32), ("warp_max", C.c_int32), ("table_cap", C.c_int32),
                 ("probe", C.c_int32), ("cta_threads", C.c_int32), ("chunk", C.c_int32),
                 ("bitmap_bits", C.c_int32), ("direct_span", C.c_int32), ("merge_ratio", C.c_int32),
-                ("merge_max", C.c_int32), ("stage", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("merge_max", C.c_int32), ("stage", C.c_int32), ("small_lanes", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class tc_ocsr_view(C.Structure):

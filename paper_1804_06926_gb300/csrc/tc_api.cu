@@ -66,7 +66,7 @@ PhaseScope::~PhaseScope() {
 }
 
 // Defaults, then TC_SMALL_MAX / TC_WARP_MAX / TC_TABLE_CAP / TC_PROBE /
-// TC_CTA_THREADS / TC_CHUNK from the environment, then non-zero fields of c.
+// TC_CTA_THREADS / TC_CHUNK / ... from the environment, then non-zero fields of c.
 static void apply_config(Tuning& t, const tc_config* c) {
     Tuning d;
     t = d;
@@ -85,6 +85,7 @@ static void apply_config(Tuning& t, const tc_config* c) {
     env("TC_MERGE_RATIO", t.merge_ratio);
     env("TC_MERGE_MAX", t.merge_max);
     env("TC_STAGE", t.stage);
+    env("TC_SMALL_LANES", t.small_lanes);
     if (!c) return;
     if (c->small_max > 0) t.small_max = c->small_max;
     if (c->small_max < 0) t.small_max = 0;  // negative disables the thread-per-edge class
@@ -101,6 +102,7 @@ static void apply_config(Tuning& t, const tc_config* c) {
     if (c->merge_ratio < 0) t.merge_ratio = 0;
     if (c->merge_max > 0) t.merge_max = c->merge_max;
     if (c->stage != 0) t.stage = c->stage > 0 ? 1 : 0;
+    if (c->small_lanes > 0) t.small_lanes = c->small_lanes;
 }
 
 static bool config_ok(const Tuning& t) {
@@ -111,7 +113,7 @@ static bool config_ok(const Tuning& t) {
            t.cta_threads % 32 == 0 && t.chunk >= 1 && t.chunk <= 32768 && t.bitmap_bits >= 0 &&
            t.bitmap_bits <= 262144 && t.bitmap_bits % 32 == 0 && t.direct_span >= 0 && t.direct_span <= 16384 &&
            (t.merge_ratio == 0 || (t.merge_ratio >= 100 && t.merge_ratio <= 1000000)) && t.merge_max >= 16 &&
-           t.merge_max <= 4096 && t.stage >= 0 && t.stage <= 1;
+           t.merge_max <= 4096 && t.stage >= 0 && t.stage <= 1 && pow2(t.small_lanes) && t.small_lanes <= 32;
 }
 
 static bool is_host_ptr(const void* p) {
@@ -278,6 +280,7 @@ tc_status tc_ctx_get_config(const tc_ctx* ctx, tc_config* out) {
     out->merge_ratio = ctx->tun.merge_ratio;
     out->merge_max = ctx->tun.merge_max;
     out->stage = ctx->tun.stage;
+    out->small_lanes = ctx->tun.small_lanes;
     return TC_OK;
 }
 

@@ -220,7 +220,7 @@ constexpr int kMpTile = kMpThreads * kMpIpt;
 // resident CTAs per SM the tile kernels are compiled for (registers permitting):
 // they wait on scattered loads, so more warps in flight hide more latency
 #ifndef TC_MP_MIN_BLOCKS
-#define TC_MP_MIN_BLOCKS 6
+#define TC_MP_MIN_BLOCKS 5
 #endif
 #ifndef TC_MP_SCATTER_MIN_BLOCKS
 #define TC_MP_SCATTER_MIN_BLOCKS 4
@@ -255,12 +255,13 @@ struct MpTile {
     int first_full;                             // local row 0 starts at j0 (it is not a continuation)
 };
 
-// Fill S for tile t.  Ends with a barrier.
+// Fill S for the tile between cut coordinates c0 and c1.  Ends with a
+// barrier.  The callers issue their loads of the tile's entries (which need
+// only c0 and c1) before this call, so that those loads are in flight while
+// the rows are laid out here.
 template <bool BATCH>
-__device__ void mp_tile(MpTile<BATCH>& S, int64_t t, int64_t n, const longlong2* __restrict__ coord,
-                        const int64_t* __restrict__ rp, const int32_t* __restrict__ row_graph,
-                        const int64_t* __restrict__ vtx_off) {
-    const longlong2 c0 = coord[t], c1 = coord[t + 1];
+__device__ void mp_tile(MpTile<BATCH>& S, longlong2 c0, longlong2 c1, int64_t n, const int64_t* __restrict__ rp,
+                        const int32_t* __restrict__ row_graph, const int64_t* __restrict__ vtx_off) {
     const int64_t i0 = c0.x, j0 = c0.y;
     const int ne = (int)(c1.y - j0);
     const int nr = (int)max((int64_t)0, min((int64_t)c1.x, n - 1) - i0 + 1);
@@ -317,6 +318,20 @@ __device__ void mp_tile(MpTile<BATCH>& S, int64_t t, int64_t n, const longlong2*
     __syncthreads();
 }
 
+// Batch mode: the first global id of the graph that owns every row of the
+// tile between cut coordinates c0 and c1, or -1 when the tile spans more
+// than one graph (graphs hold tens of thousands of entries, tiles 2048 items,
+// so almost every tile lies inside one graph).  Needs no shared state, so a
+// tile kernel can offset and gather its entries before mp_tile.
+__device__ __forceinline__ int64_t tile_graph_base(longlong2 c0, longlong2 c1, int64_t n,
+                                                   const int32_t* __restrict__ row_graph,
+                                                   const int64_t* __restrict__ vtx_off) {
+    if (n <= 0) return -1;
+    const int64_t ia = min((int64_t)c0.x, n - 1), ib = min((int64_t)c1.x, n - 1);
+    const int32_t ga = row_graph[ia];
+    return ga == row_graph[ib] ? vtx_off[ga] : -1;
+}
+
 // OR the ballot of 32 consecutive entries starting at global index g into a bitmask.
 __device__ __forceinline__ void or_bits(unsigned* __restrict__ mask, int64_t g, unsigned bal) {
     if (!bal) return;
@@ -371,19 +386,39 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(i
     __shared__ MpTile<BATCH> S;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        mp_tile<BATCH>(S, t, n, coord, rp, row_graph, vtx_off);
-        const int64_t i0 = S.i0, j0 = S.j0;
-        const int ne = S.ne, nr = S.nr;
-        // all loads of the tile first (8 independent streams, then 8 gathers)
+        const longlong2 c0 = coord[t], c1 = coord[t + 1];
+        const int64_t j0 = c0.y;
+        const int ne = (int)(c1.y - j0);
+        // the tile's entries and their degree gathers first (8 independent
+        // streams, then 8 gathers), in flight while mp_tile lays out the rows
         int32_t vv[kMpIpt];
         int dv[kMpIpt];
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
-            vv[q] = e < ne ? col[j0 + e] + (BATCH ? S.base[S.row[e]] : 0) : 0;
+            vv[q] = e < ne ? col[j0 + e] : 0;
         }
+        // batch: local ids become global with the graph's base, known here
+        // when the whole tile lies in one graph
+        const int64_t gbase = BATCH ? tile_graph_base(c0, c1, n, row_graph, vtx_off) : 0;
+        if (gbase >= 0) {
 #pragma unroll
-        for (int q = 0; q < kMpIpt; ++q) dv[q] = q * kMpThreads + (int)threadIdx.x < ne ? deg[vv[q]] : 0;
+            for (int q = 0; q < kMpIpt; ++q) {
+                if (BATCH) vv[q] += (int32_t)gbase;
+                dv[q] = q * kMpThreads + (int)threadIdx.x < ne ? deg[vv[q]] : 0;
+            }
+        }
+        mp_tile<BATCH>(S, c0, c1, n, rp, row_graph, vtx_off);
+        const int64_t i0 = S.i0;
+        if (BATCH && gbase < 0) {  // the tile spans graphs: each entry takes its row's base
+#pragma unroll
+            for (int q = 0; q < kMpIpt; ++q) {
+                const int e = q * kMpThreads + threadIdx.x;
+                if (e < ne) vv[q] += S.base[S.row[e]];
+            }
+#pragma unroll
+            for (int q = 0; q < kMpIpt; ++q) dv[q] = q * kMpThreads + (int)threadIdx.x < ne ? deg[vv[q]] : 0;
+        }
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
@@ -443,9 +478,38 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
     if (threadIdx.x == 0) { s_piv = 0; s_small = 0; }
     unsigned long long my_piv = 0, my_small = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        mp_tile<BATCH>(S, t, n, coord, rp, row_graph, vtx_off);
-        const int64_t i0 = S.i0, j0 = S.j0;
-        const int ne = S.ne, nr = S.nr;
+        const longlong2 c0 = coord[t], c1 = coord[t + 1];
+        const int64_t j0 = c0.y;
+        const int ne = (int)(c1.y - j0);
+        // the tile's keep bits and entries, and the (rank, d+) gathers of the
+        // kept ones, first: in flight while mp_tile lays out the rows
+        unsigned kmask = 0;  // bit q: entry q is kept
+        int32_t vv[kMpIpt];
+        int rr[kMpIpt], bb[kMpIpt];
+#pragma unroll
+        for (int q = 0; q < kMpIpt; ++q) {
+            const int e = q * kMpThreads + threadIdx.x;
+            vv[q] = 0;
+            rr[q] = bb[q] = 0;
+            if (e < ne) {
+                const int64_t g = j0 + e;
+                kmask |= ((keep[g >> 5] >> (g & 31)) & 1u) << q;
+                vv[q] = col[g];
+            }
+        }
+        const int64_t gbase = BATCH ? tile_graph_base(c0, c1, n, row_graph, vtx_off) : 0;
+        if (gbase >= 0) {  // batch: the whole tile lies in one graph
+#pragma unroll
+            for (int q = 0; q < kMpIpt; ++q) {
+                if (BATCH) vv[q] += (int32_t)gbase;
+                const int2 rv = (kmask >> q) & 1u ? rd2[vv[q]] : make_int2(0, 0);
+                rr[q] = rv.x;
+                bb[q] = rv.y;
+            }
+        }
+        mp_tile<BATCH>(S, c0, c1, n, rp, row_graph, vtx_off);
+        const int64_t i0 = S.i0;
+        const int nr = S.nr;
         // colr position of a kept entry = its colp position + colr_row(u) - rpp[u]
         // = pos + 3u + 3 - r, r = (rpp[u] + 3u + 3) mod 4 (kept in du, which is
         // not needed here; the offset itself exceeds 32 bits for large u).
@@ -456,40 +520,37 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
             S.cs[k] = rd2[u].y;
         }
         __syncthreads();
-        // all loads of the tile first: keep words and lists, then the rank gathers
-        unsigned kw[kMpIpt];
-        int32_t vv[kMpIpt];
-        int rr[kMpIpt];
+        if (BATCH && gbase < 0) {  // the tile spans graphs: each entry takes its row's base
 #pragma unroll
-        for (int q = 0; q < kMpIpt; ++q) {
-            const int e = q * kMpThreads + threadIdx.x;
-            kw[q] = 0;
-            vv[q] = 0;
-            if (e < ne) {
-                const int64_t g = j0 + e;
-                kw[q] = (keep[g >> 5] >> (g & 31)) & 1u;
-                vv[q] = col[g] + (BATCH ? S.base[S.row[e]] : 0);
+            for (int q = 0; q < kMpIpt; ++q) {
+                const int e = q * kMpThreads + threadIdx.x;
+                if (e < ne) vv[q] += S.base[S.row[e]];
             }
-        }
-        int bb[kMpIpt];
 #pragma unroll
-        for (int q = 0; q < kMpIpt; ++q) {
-            const int2 rv = kw[q] ? rd2[vv[q]] : make_int2(0, 0);
-            rr[q] = rv.x;
-            bb[q] = rv.y;
+            for (int q = 0; q < kMpIpt; ++q) {
+                const int2 rv = (kmask >> q) & 1u ? rd2[vv[q]] : make_int2(0, 0);
+                rr[q] = rv.x;
+                bb[q] = rv.y;
+            }
         }
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
             const bool valid = e < ne;
-            int64_t pos = 0;
+            const bool kq = (kmask >> q) & 1u;
+            // the warp's 32 entries are consecutive, so its kept ones sit at
+            // consecutive positions from the first one's: p0 + the kept lanes below
+            const unsigned kb = __ballot_sync(0xffffffffu, kq && valid);
+            int64_t p0 = 0, pos = 0;
+            if (kb) {
+                p0 = bits_before(keep, kpre, j0 + q * kMpThreads + (threadIdx.x & ~31u));  // the same for the warp
+                pos = p0 + __popc(kb & ((1u << lane) - 1u));
+            }
             bool pu = false, pv = false, mg = false;
             int mu = 0;
             if (valid) {
                 const int k = S.row[e];
-                if (kw[q]) {
-                    const int64_t g = j0 + e;
-                    pos = bits_before(keep, kpre, g);
+                if (kq) {
                     colp[pos] = vv[q];
                     colr[pos + 3 * (i0 + k) + 3 - S.du[k]] = rr[q];
                     // a-4 classification of the oriented edge (u, v) at position pos
@@ -505,7 +566,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                 }
             }
             // merge-class edges are appended to their list, one atomic per warp
-            const unsigned mb = __ballot_sync(0xffffffffu, mg);
+            const unsigned mb = merge_ratio > 0 ? __ballot_sync(0xffffffffu, mg) : 0u;
             if (mb) {
                 const int lead = __ffs(mb) - 1;
                 unsigned long long base = 0;
@@ -514,16 +575,13 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                 const unsigned long long at = base + __popc(mb & ((1u << lane) - 1u));
                 if (mg && at < (unsigned long long)medge_cap) medge[at] = make_int2(mu, vv[q]);
             }
-            // the warp's kept entries sit at consecutive positions: one bit
-            // pattern per mask, placed at the first kept entry's position
-            const unsigned kb = __ballot_sync(0xffffffffu, kw[q] != 0 && valid);
+            // one bit pattern per mask, placed at the first kept entry's position
             if (kb) {
                 const unsigned lt = (1u << lane) - 1u;
                 const int idx = __popc(kb & lt);
                 const unsigned ub = __reduce_or_sync(0xffffffffu, pu ? (1u << idx) : 0u);
                 const unsigned vb2 = __reduce_or_sync(0xffffffffu, pv ? (1u << idx) : 0u);
                 const int first = __ffs(kb) - 1;
-                const int64_t p0 = __shfl_sync(0xffffffffu, pos, first);
                 if (lane == first) {
                     or_bits(umask, p0, ub);
                     or_bits(vmask, p0, vb2);
@@ -681,7 +739,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_sc
                                                               int32_t* __restrict__ pcol) {
     __shared__ MpTile<false> S;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        mp_tile<false>(S, t, n, coord, rpp, nullptr, nullptr);
+        mp_tile<false>(S, coord[t], coord[t + 1], n, rpp, nullptr, nullptr);
         const int64_t i0 = S.i0, j0 = S.j0;
         const int ne = S.ne;
         unsigned uw[kMpIpt], vw[kMpIpt];
@@ -743,6 +801,7 @@ __global__ void k_pdesc(const unsigned long long* __restrict__ n_pivot, const in
 // (segment of the pivot list, chunk_c partners); a segment holds at most
 // table_cap keys.
 __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ dp,
+                                               const int32_t* __restrict__ deg, int small_max,
                                                const int64_t* __restrict__ prp,
                                                int warp_max, int table_cap, int chunk, int chunk_c,
                                                Item* __restrict__ iw, int64_t iw_cap,
@@ -751,6 +810,10 @@ __global__ void __launch_bounds__(256) k_items(int64_t n, const int32_t* __restr
     __shared__ long long sm[33];
     __shared__ unsigned long long s_bw, s_bc;
     for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < n; t0 += (int64_t)gridDim.x * blockDim.x) {
+        // A pivot's list is longer than small_max, so its degree is too.  The
+        // degree does not increase along descending rank: once the block's
+        // first vertex has degree <= small_max, no later one is a pivot.
+        if (deg[perm[n - 1 - t0]] <= small_max) break;  // the same address for the whole block
         // pivots in descending rank order: pivots of similar rank share many
         // partners, so the partner lists that concurrent items stream stay in L2
         const int64_t r = t0 + threadIdx.x;
@@ -1044,7 +1107,8 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     dev_free(rd2, s); dev_free(pd2, s); dev_free(vtop, s);
     if (n > 0) {
         PhaseScope ph(ctx, kPhItems, s);
-        k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->perm, o->dplus, o->prp, tun.warp_max, tun.table_cap, tun.chunk,
+        k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->perm, o->dplus, o->deg, tun.small_max, o->prp, tun.warp_max,
+                                                     tun.table_cap, tun.chunk,
                                                      (int)chunk_c,
                                                      o->items_warp, o->items_warp_cap, o->items_cta, o->items_cta_cap, o->dc);
         TC_LAUNCH(ctx);

@@ -44,6 +44,7 @@ struct Tuning {
     int merge_ratio = 0;       // percent; balanced edges (max/min d+ <= ratio, max <= merge_max) merge; 0 = off
     int merge_max = 256;
     int stage = 0;             // CTA kernel: 1 = lists of >= 4 lanes per partner staged by the copy engine; 0 = per-lane loads
+    int small_lanes = 1;       // threads per row of the thread-merge class (power of two, <= 32)
 };
 
 }  // namespace tc

@@ -138,6 +138,11 @@ CONFIGS = [
     dict(merge_ratio=100, merge_max=16),
     dict(merge_ratio=1000000, merge_max=4096),
     dict(merge_ratio=400, small_max=-1, warp_max=8),
+    # threads per row of the thread-merge class
+    dict(small_lanes=4),
+    dict(small_lanes=32, small_max=64, warp_max=64),
+    dict(small_lanes=2, small_max=16, merge_ratio=200),
+    dict(small_lanes=8, small_max=32),
 ]
 
 
@@ -285,3 +290,14 @@ def test_many_counts_on_one_handle(ctx):
         assert int(tot.item()) == T
         np.testing.assert_array_equal(pv.cpu().numpy(), t)
     o.free()
+
+
+def test_config_out_of_range_is_refused(B):
+    for bad in (dict(small_lanes=3), dict(small_lanes=64), dict(table_cap=100), dict(merge_ratio=50)):
+        with pytest.raises(B.TCError) as ei:
+            B.Context(0, **bad)
+        assert ei.value.status == B.TC_ERR_INVALID_ARG, bad
+    c = B.Context(0, small_lanes=8)
+    got = c.get_config()
+    assert got["small_lanes"] == 8
+    c.close()
