@@ -49,8 +49,15 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long* sm,
     return r;
 }
 
+// skip (nullable): a device count; when it is zero the scan is not needed
+// (its input is all zeros and its consumers skip too) and every kernel of
+// the scan returns at once.
+__device__ __forceinline__ bool scan_skipped(const unsigned long long* skip) { return skip && *skip == 0ull; }
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __restrict__ in, int64_t n,
-                                                              long long* __restrict__ tile_sum) {
+                                                              long long* __restrict__ tile_sum,
+                                                              const unsigned long long* __restrict__ skip) {
+    if (scan_skipped(skip)) return;
     __shared__ long long sm[33];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     long long s = 0;
@@ -65,7 +72,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __r
 }
 
 __global__ void __launch_bounds__(1024) k_scan_sums(long long* __restrict__ tile_sum, int64_t ntiles,
-                                                    int64_t* __restrict__ out, int64_t n) {
+                                                    int64_t* __restrict__ out, int64_t n,
+                                                    const unsigned long long* __restrict__ skip) {
+    if (scan_skipped(skip)) return;
     __shared__ long long sm[33];
     long long carry = 0;
     for (int64_t b = 0; b < ntiles; b += blockDim.x) {
@@ -81,7 +90,9 @@ __global__ void __launch_bounds__(1024) k_scan_sums(long long* __restrict__ tile
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* __restrict__ in, int64_t n,
                                                              const long long* __restrict__ tile_off,
-                                                             int64_t* __restrict__ out) {
+                                                             int64_t* __restrict__ out,
+                                                             const unsigned long long* __restrict__ skip) {
+    if (scan_skipped(skip)) return;
     __shared__ long long sm[33];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int32_t v[kScanItems];
@@ -105,15 +116,21 @@ size_t scan_tmp_bytes(int64_t n) {
     return (size_t)std::max<int64_t>(nt, 1) * sizeof(long long);
 }
 
-cudaError_t scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* tmp, size_t tmp_bytes,
-                            cudaStream_t s) {
+// scan_i32_to_i64 that does nothing (out left unwritten) when *skip (device) is 0
+static cudaError_t scan_i32_to_i64_unless_zero(const int32_t* in, int64_t* out, int64_t n, void* tmp,
+                                               size_t tmp_bytes, cudaStream_t s, const unsigned long long* skip) {
     int64_t nt = (n + kScanTile - 1) / kScanTile;
     if (tmp_bytes < scan_tmp_bytes(n)) return cudaErrorInvalidValue;
     long long* ts = (long long*)tmp;
-    if (nt > 0) k_scan_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, ts);
-    k_scan_sums<<<1, 1024, 0, s>>>(ts, nt, out, n);
-    if (nt > 0) k_scan_apply<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, ts, out);
+    if (nt > 0) k_scan_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, ts, skip);
+    k_scan_sums<<<1, 1024, 0, s>>>(ts, nt, out, n, skip);
+    if (nt > 0) k_scan_apply<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, ts, out, skip);
     return cudaGetLastError();
+}
+
+cudaError_t scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* tmp, size_t tmp_bytes,
+                            cudaStream_t s) {
+    return scan_i32_to_i64_unless_zero(in, out, n, tmp, tmp_bytes, s, nullptr);
 }
 
 // ============================================================================
@@ -716,9 +733,17 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const 
 
 // prp[p] = U(rpp[p]) + Vpre(p), p = 0 .. n; vtop[p] = prp[p+1], the end of
 // p's V-part, which the scatter counts down from
+// With no pivot edge at all (n_pivot = 0: a graph of short lists only) the
+// masks, counts and scans are all zero and were skipped: prp is all zeros.
 __global__ void k_pivot_offsets(int64_t n, const int64_t* __restrict__ rpp, const unsigned* __restrict__ umask,
                                 const int64_t* __restrict__ upre, const int64_t* __restrict__ vpre,
-                                int64_t* __restrict__ prp, unsigned long long* __restrict__ vtop) {
+                                int64_t* __restrict__ prp, unsigned long long* __restrict__ vtop,
+                                const unsigned long long* __restrict__ n_pivot) {
+    if (*n_pivot == 0ull) {
+        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += (int64_t)gridDim.x * blockDim.x)
+            prp[p] = 0;
+        return;
+    }
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = bits_before(umask, upre, rpp[p]) + vpre[p];
         prp[p] = o;
@@ -736,7 +761,9 @@ __global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_sc
                                                               const unsigned* __restrict__ umask, const unsigned* __restrict__ vmask,
                                                               const int64_t* __restrict__ upre, const int64_t* __restrict__ vpre,
                                                               unsigned long long* __restrict__ vtop,
-                                                              int32_t* __restrict__ pcol) {
+                                                              int32_t* __restrict__ pcol,
+                                                              const unsigned long long* __restrict__ n_pivot) {
+    if (*n_pivot == 0ull) return;  // no pivot edge: nothing to place
     __shared__ MpTile<false> S;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         mp_tile<false>(S, coord[t], coord[t + 1], n, rpp, nullptr, nullptr);
@@ -1086,16 +1113,20 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     }
     {
         PhaseScope ph(ctx, kPhPivotScan, s);
+        // with no pivot edge (n_pivot_edges = 0) the masks and counts are all
+        // zero: the scans return at once and prp is written as zeros
+        const unsigned long long* np = &o->dc->n_pivot_edges;
         k_popc<<<grid_for(uw, 256, ns), 256, 0, s>>>(umask, uw, wpc);
-        scan_i32_to_i64(wpc, upre, uw, wtmp, wtb, s);
-        scan_i32_to_i64(pc, vpre, n, wtmp, wtb, s);
-        k_pivot_offsets<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, o->rpp, umask, upre, vpre, o->prp, vtop);
+        scan_i32_to_i64_unless_zero(wpc, upre, uw, wtmp, wtb, s, np);
+        scan_i32_to_i64_unless_zero(pc, vpre, n, wtmp, wtb, s, np);
+        k_pivot_offsets<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, o->rpp, umask, upre, vpre, o->prp, vtop, np);
         ctx->launches += 8;
     }
     {
         PhaseScope ph(ctx, kPhPivotScatter, s);
         if (nt2 > 0) {
-            k_pivot_scatter<<<g2, kMpThreads, 0, s>>>(n, nt2, coord, o->rpp, o->colp, umask, vmask, upre, vpre, vtop, o->pcol);
+            k_pivot_scatter<<<g2, kMpThreads, 0, s>>>(n, nt2, coord, o->rpp, o->colp, umask, vmask, upre, vpre, vtop, o->pcol,
+                                                      &o->dc->n_pivot_edges);
             TC_LAUNCH(ctx);
             // the partners' descriptors beside pcol, in one coalesced pass
             k_pdesc<<<grid_for(m, 256, ns), 256, 0, s>>>(&o->dc->n_pivot_edges, o->pcol, pd2, o->pdesc);
