@@ -159,8 +159,15 @@ __global__ void k_rank_keys(int64_t n, const int32_t* __restrict__ deg, int b, u
         keys[v] = ((unsigned long long)deg[v] << b) | (unsigned long long)v;
 }
 
-__global__ void k_rank_from_sorted(int64_t n, const unsigned long long* __restrict__ sorted, int b,
+// The sort ran 8-bit passes over the degree bits [b, 2b) of the keys; the
+// passes above the highest set bit of the maximum degree did nothing, so the
+// keys are in ka after an even number of real passes, in kb after an odd one.
+__global__ void k_rank_from_sorted(int64_t n, const unsigned long long* __restrict__ ka,
+                                   const unsigned long long* __restrict__ kb, const int* __restrict__ max_deg, int b,
                                    int32_t* __restrict__ rank, int32_t* __restrict__ perm) {
+    int real = 0;
+    for (int shift = b; shift < 2 * b; shift += 8) real += ((unsigned)*max_deg >> (shift - b)) != 0u;
+    const unsigned long long* __restrict__ sorted = (real & 1) ? kb : ka;
     const unsigned long long mask = (1ull << b) - 1ull;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = (int32_t)(sorted[r] & mask);
@@ -1000,7 +1007,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
             // the keys are written in id order and the sort is stable, so
             // sorting the degree bits alone yields (degree, id) order
             radix_sort_u64(ka, kb, n, 2 * b, s, &sorted, &ctx->launches, b, &o->dc->max_deg, b);
-            k_rank_from_sorted<<<grid_for(n, 256, ns), 256, 0, s>>>(n, sorted, b, o->rank, o->perm);
+            k_rank_from_sorted<<<grid_for(n, 256, ns), 256, 0, s>>>(n, ka, kb, &o->dc->max_deg, b, o->rank, o->perm);
             ctx->launches += 2;
         }
         dev_free(ka, s);

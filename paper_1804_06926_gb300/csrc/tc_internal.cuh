@@ -162,7 +162,8 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
 
 // Stable LSD radix sort of uint64 keys on bits [low_bit, key_bits).  With
 // maxv (device), bits [vbase, ...) of every key are at most *maxv, and the
-// passes over digits that are then zero for all keys reduce to copies.
+// passes over digits that are then zero for all keys do nothing: the result
+// is then in ka after an even number of real passes, in kb after an odd one.
 cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64_t K, int key_bits, cudaStream_t s,
                            unsigned long long** sorted, long long* launches, int low_bit,
                            const int* maxv = nullptr, int vbase = 0);

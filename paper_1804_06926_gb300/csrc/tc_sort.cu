@@ -40,7 +40,9 @@ __global__ void k_make_keys(int64_t np, const int32_t* __restrict__ src, const i
 
 // A pass is trivial when every key's digit is 0: with maxv given, digit
 // bits [shift, shift+8) of a key are bits [shift-vbase, ...) of a value that
-// is at most *maxv.  A trivial pass is the identity and is done as a copy.
+// is at most *maxv.  A trivial pass is the identity and does nothing.  The
+// trivial passes are the last ones (a digit above the highest set bit of
+// *maxv), so the keys end in the buffer that the last real pass wrote.
 __device__ __forceinline__ bool rs_trivial(const int* maxv, int vbase, int shift) {
     return maxv && shift >= vbase && ((unsigned)*maxv >> (shift - vbase)) == 0u;
 }
@@ -71,14 +73,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long l
     __shared__ int run[256];
     __shared__ long long base[256];
     const int tid = threadIdx.x, warp = tid >> 5;
-    if (rs_trivial(maxv, vbase, shift)) {
-        const int64_t t0 = (int64_t)blockIdx.x * kRsTile;
-        for (int r = 0; r < kRsItems; ++r) {
-            const int64_t i = t0 + r * kRsThreads + tid;
-            if (i < K) out[i] = in[i];
-        }
-        return;
-    }
+    if (rs_trivial(maxv, vbase, shift)) return;
     run[tid] = 0;
     base[tid] = off[(int64_t)tid * ntiles + blockIdx.x];
     __syncthreads();
@@ -112,9 +107,12 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long l
 }
 
 // LSD radix sort of K keys on bits [low_bit, key_bits) (8 bits per pass,
-// stable).  ka holds the input, kb is scratch of the same size; *sorted
-// receives whichever of the two holds the result (a pass made trivial by
-// maxv still copies, so the ping-pong order never depends on device data).
+// stable).  ka holds the input, kb is scratch of the same size.  Without
+// maxv, *sorted receives whichever of the two holds the result.  With maxv,
+// the passes made trivial by it do nothing, so the result is in ka after an
+// even number of real passes and in kb after an odd one, which only the
+// device knows: *sorted receives ka, and the consumer counts the real passes
+// from *maxv to pick the buffer (k_rank_from_sorted in tc_build.cu).
 cudaError_t radix_sort_u64(unsigned long long* ka, unsigned long long* kb, int64_t K, int key_bits, cudaStream_t s,
                            unsigned long long** sorted, long long* launches, int low_bit, const int* maxv, int vbase) {
     *sorted = ka;
