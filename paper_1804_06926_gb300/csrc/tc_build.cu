@@ -531,6 +531,16 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
                 bb[q] = rv.y;
             }
         }
+        // the first row of this thread's share of the tile's rows: its rpp
+        // and d+ loads, too, need only the cut coordinates
+        const int64_t ia = c0.x;
+        const int nr0 = (int)max((int64_t)0, min((int64_t)c1.x, n - 1) - ia + 1);
+        int r3 = 0, dr = 0;
+        if ((int)threadIdx.x < nr0) {
+            const int64_t u = ia + threadIdx.x;
+            r3 = (int)((rpp[u] + 3 * u + 3) & 3);
+            dr = rd2[u].y;
+        }
         mp_tile<BATCH>(S, c0, c1, n, rp, row_graph, vtx_off);
         const int64_t i0 = S.i0;
         const int nr = S.nr;
@@ -538,7 +548,11 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
         // = pos + 3u + 3 - r, r = (rpp[u] + 3u + 3) mod 4 (kept in du, which is
         // not needed here; the offset itself exceeds 32 bits for large u).
         // cs, used only to find each entry's row, now holds d+ of the row.
-        for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+        if ((int)threadIdx.x < nr) {
+            S.du[threadIdx.x] = r3;
+            S.cs[threadIdx.x] = dr;
+        }
+        for (int k = threadIdx.x + blockDim.x; k < nr; k += blockDim.x) {
             const int64_t u = i0 + k;
             S.du[k] = (int)((rpp[u] + 3 * u + 3) & 3);
             S.cs[k] = rd2[u].y;

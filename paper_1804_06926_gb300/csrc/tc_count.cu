@@ -1218,8 +1218,13 @@ __global__ void __launch_bounds__(256, TC_WARP_MIN_BLOCKS) k_count_warp(CountArg
 // thread per row), lane j of the group merging the row's edges j, j+L, ...:
 // a sorted merge of two short vertex-id rows per edge.  The kernel needs few
 // registers, so many resident threads hide the latency of the merge's loads.
+// STEP (chosen per launch, small_max > 8): a branch-free merge step that
+// carries both current elements and reloads only the side that moved.  On
+// lists of up to 32 entries (BA graphs) it takes count_small from 17.4 to
+// 14.8 ms; on lists of at most 8 the plain loop is as fast (R-MAT s22) or
+// faster (a grid's 1-5 entries: 0.47 against 0.57 ms).
 // ---------------------------------------------------------------------------
-template <bool PV>
+template <bool PV, bool STEP>
 __global__ void __launch_bounds__(256) k_count_small(CountArgs a) {
     __shared__ unsigned long long s_acc;
     if (threadIdx.x == 0) s_acc = 0;
@@ -1243,15 +1248,28 @@ __global__ void __launch_bounds__(256) k_count_small(CountArgs a) {
             const int64_t vb = a.rpp[v];
             if (!dbg_ok(ub + du <= a.colp_len && vb + dv <= a.colp_len, TC_DEVERR_BOUNDS)) continue;
             int x = 0, y = 0, c = 0;
-            while (x < du && y < dv) {
-                const int xa = a.colp[ub + x], yb = a.colp[vb + y];
-                if (xa < yb) ++x;
-                else if (xa > yb) ++y;
-                else {
-                    ++c;
-                    if (PV) atomicAdd(&a.t[xa], 1ull);
-                    ++x;
-                    ++y;
+            if (STEP) {  // both lists are non-empty here: d+(u) >= 2, d+(v) >= 1
+                int xa = a.colp[ub], yb = a.colp[vb];
+                while (x < du && y < dv) {
+                    const bool eq = xa == yb, ax = xa <= yb, ay = yb <= xa;
+                    if (PV && eq) atomicAdd(&a.t[xa], 1ull);
+                    c += eq;
+                    x += ax;
+                    y += ay;
+                    if (ax && x < du) xa = a.colp[ub + x];
+                    if (ay && y < dv) yb = a.colp[vb + y];
+                }
+            } else {
+                while (x < du && y < dv) {
+                    const int xa = a.colp[ub + x], yb = a.colp[vb + y];
+                    if (xa < yb) ++x;
+                    else if (xa > yb) ++y;
+                    else {
+                        ++c;
+                        if (PV) atomicAdd(&a.t[xa], 1ull);
+                        ++x;
+                        ++y;
+                    }
                 }
             }
             if (c) {
@@ -1459,13 +1477,13 @@ tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals
         PhaseScope ph(ctx, kPhCountSmall, s);
         TC_LAUNCH(ctx);
         int per_sm = 0;
-        if (per_vertex) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_small<true>, 256, 0);
-            k_count_small<true><<<(unsigned)(ns * std::max(per_sm, 1)), 256, 0, s>>>(a);
-        } else {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_small<false>, 256, 0);
-            k_count_small<false><<<(unsigned)(ns * std::max(per_sm, 1)), 256, 0, s>>>(a);
-        }
+        auto launch = [&](auto kern) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+            kern<<<(unsigned)(ns * std::max(per_sm, 1)), 256, 0, s>>>(a);
+        };
+        const bool step = tun.small_max > 8;  // longer lists: the branch-free merge step
+        if (per_vertex) step ? launch(k_count_small<true, true>) : launch(k_count_small<true, false>);
+        else step ? launch(k_count_small<false, true>) : launch(k_count_small<false, false>);
     }
     if (o->medge) {
         PhaseScope ph(ctx, kPhCountMerge, s);
