@@ -168,6 +168,28 @@ def test_merge_class_takes_the_balanced_edges(B):
 
 
 # ---------------------------------------------------------------- closed forms, edge cases
+@pytest.mark.parametrize("D,n", [(255, 256), (255, 70000), (300, 70000), (65535, 70000), (65536, 70000)])
+def test_rank_sort_digit_passes(B, D, n):
+    """The (degree, id) rank comes from a radix sort over the degree's 8-bit
+    digits whose passes above the largest degree's top bit do nothing, so the
+    sorted keys end in one buffer or the other by the number of real passes.
+    A hub of degree D just below and above 2^8 and 2^16, with n up to 70,000
+    (17 id bits), gives one, two and three real passes, with and without
+    passes left out.  A wrong buffer scrambles the rank ids of the oriented
+    lists, which the table kernels key on: the per-vertex counts of the
+    clique's pivots (warp tables by default, CTA tables with warp_max 8) would
+    differ from the oracle's."""
+    edges = [(0, i) for i in range(1, D + 1)]
+    edges += [(i, i + 1) for i in range(1, D)]  # triangles (0, i, i + 1)
+    edges += [(i, j) for i in range(1, 41) for j in range(i + 2, 41)]  # with the path, a clique on 1..40
+    g = graph_from_edges(n, edges)
+    assert int(np.diff(g.row_ptr).max()) == D
+    for cfg in ({}, dict(warp_max=8)):
+        c = B.Context(0, **cfg)
+        assert_parity(c, g)
+        c.close()
+
+
 @pytest.mark.parametrize("n", [3, 4, 33, 200])
 def test_complete_graph(ctx, n):
     g = graph_from_edges(n, list(itertools.combinations(range(n), 2)))
