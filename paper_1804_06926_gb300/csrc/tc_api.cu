@@ -300,11 +300,29 @@ tc_status tc_build_oriented_csr(tc_ctx* ctx, const tc_graph* g, tc_ocsr** out, v
         const int32_t* col = g->col;
         int64_t* drp = nullptr;
         int32_t* dcol = nullptr;
+        const int32_t* col_src = nullptr;
         if (host) {
             if (g->row_ptr[0] != 0 || g->row_ptr[g->n] != g->nnz)
                 return set_err(ctx, TC_ERR_INVALID_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] must be nnz");
             cudaError_t e = upload(g->row_ptr, g->n + 1, &drp, s);
-            if (e == cudaSuccess) e = upload(g->col, g->nnz, &dcol, s);
+            // A pinned, mapped col (cudaHostAlloc, or registered and mapped)
+            // is read by the orientation's first pass straight from host
+            // memory, which leaves the device copy: the transfer (host to
+            // device runs at the same rate either way) overlaps that pass
+            // instead of preceding it.  Pageable memory, and validation
+            // (which reads col before that pass), take the plain upload.
+            if (e == cudaSuccess && g->nnz > 0 && !validate) {
+                cudaPointerAttributes at;
+                if (cudaPointerGetAttributes(&at, g->col) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                    at.devicePointer)
+                    col_src = static_cast<const int32_t*>(at.devicePointer);
+                else
+                    cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                if (col_src) e = dev_alloc((void**)&dcol, sizeof(int32_t) * (size_t)g->nnz, s);
+                else e = upload(g->col, g->nnz, &dcol, s);
+            }
             if (e != cudaSuccess) {
                 dev_free(drp, s);
                 dev_free(dcol, s);
@@ -313,7 +331,7 @@ tc_status tc_build_oriented_csr(tc_ctx* ctx, const tc_graph* g, tc_ocsr** out, v
             rp = drp;
             col = dcol;
         }
-        tc_status st = build_from_device_csr(ctx, g->n, g->nnz, rp, col, nullptr, 0, validate, out, s);
+        tc_status st = build_from_device_csr(ctx, g->n, g->nnz, rp, col, nullptr, 0, validate, out, s, col_src);
         dev_free(drp, s);
         dev_free(dcol, s);
         return st;

@@ -406,7 +406,8 @@ template <bool BATCH>
 __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(int64_t n, int64_t ntiles, const longlong2* __restrict__ coord,
                                                              const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                              const int32_t* __restrict__ deg, const int32_t* __restrict__ row_graph,
-                                                             const int64_t* __restrict__ vtx_off, unsigned* __restrict__ keep) {
+                                                             const int64_t* __restrict__ vtx_off, unsigned* __restrict__ keep,
+                                                             int32_t* __restrict__ col_copy) {
     __shared__ MpTile<BATCH> S;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -421,6 +422,13 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(i
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
             vv[q] = e < ne ? col[j0 + e] : 0;
+        }
+        if (col_copy) {  // col is the caller's pinned host array: leave a device copy for the later passes
+#pragma unroll
+            for (int q = 0; q < kMpIpt; ++q) {
+                const int e = q * kMpThreads + threadIdx.x;
+                if (e < ne) col_copy[j0 + e] = vv[q];
+            }
         }
         // batch: local ids become global with the graph's base, known here
         // when the whole tile lies in one graph
@@ -913,7 +921,9 @@ static int64_t isqrt_bound(int64_t x) {
 }
 
 tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
-                                const int64_t* vtx_off, int64_t G, bool validate, tc_ocsr** out, cudaStream_t s) {
+                                const int64_t* vtx_off, int64_t G, bool validate, tc_ocsr** out, cudaStream_t s,
+                                const int32_t* col_src) {
+    if (col_src && (vtx_off || validate)) return set_err(ctx, TC_ERR_INVALID_ARG, "internal: col_src with a batch or validation");
     const Tuning tun = ctx->tun;
     const bool batch = vtx_off != nullptr;
     const int64_t m = nnz / 2;
@@ -1079,8 +1089,12 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         cudaMemsetAsync(keep, 0, sizeof(unsigned) * kw, s);
         k_mp_coords<<<grid_for(nt1 + 1, 256, ns), 256, 0, s>>>(n, nnz, row_ptr, nt1, coord);
         if (nt1 > 0) {
-            if (batch) k_orient_flags<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, o->row_graph, vtx_off, keep);
-            else k_orient_flags<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, nullptr, nullptr, keep);
+            if (batch) k_orient_flags<true><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, o->row_graph, vtx_off, keep,
+                                                                       nullptr);
+            else if (col_src)  // reads the pinned host entries and leaves their device copy in col
+                k_orient_flags<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col_src, deg, nullptr, nullptr, keep,
+                                                                const_cast<int32_t*>(col));
+            else k_orient_flags<false><<<g1, kMpThreads, 0, s>>>(n, nt1, coord, row_ptr, col, deg, nullptr, nullptr, keep, nullptr);
         }
         ctx->launches += 2;
     }

@@ -156,9 +156,12 @@ size_t scan_tmp_bytes(int64_t n);
 
 // Build the oriented CSR and its partition from a device CSR (rows may be a
 // batch: row_graph/vtx_off non-null map local neighbour ids to global ones).
+// col_src (single graph, no validation): the entries are read from this
+// device-accessible address of a pinned host array by the first pass over
+// them, which writes them into col, then a device buffer of nnz entries.
 tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr,
                                 const int32_t* col, const int64_t* vtx_off, int64_t G,
-                                bool validate, tc_ocsr** out, cudaStream_t s);
+                                bool validate, tc_ocsr** out, cudaStream_t s, const int32_t* col_src = nullptr);
 
 // Stable LSD radix sort of uint64 keys on bits [low_bit, key_bits).  With
 // maxv (device), bits [vbase, ...) of every key are at most *maxv, and the

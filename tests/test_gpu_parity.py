@@ -248,6 +248,36 @@ def test_host_inputs_and_outputs(ctx):
     assert Th == T and (th == t).all()
 
 
+def test_pinned_host_inputs(ctx):
+    """A pinned host CSR (torch pin_memory: page-locked and mapped for the
+    device) is read by the orientation's first pass straight from host
+    memory, which leaves the device copy the later passes use.  The oriented
+    CSR and the counts equal the oracle's, with host and with device outputs;
+    with validation (which reads the input first) the plain upload is taken."""
+    for g in (gen.rmat(12, 16, seed=5), gen.grid(60, 70, seed=1), gen.ba(2000, 7, seed=2)):
+        rp = torch.from_numpy(g.row_ptr).pin_memory()
+        col = torch.from_numpy(g.col).pin_memory()
+        orp, ocol = oracle.orient(g.n, g.row_ptr, g.col)
+        T, t = oracle.count(g.n, g.row_ptr, g.col)
+        for validate in (False, True):
+            for host_out in (True, False):
+                o = ctx.build(g.n, rp, col, validate=validate)
+                hrp, hcol = o.copy_to_host()
+                np.testing.assert_array_equal(hrp, orp)
+                np.testing.assert_array_equal(hcol, ocol)
+                dev_ = "cpu" if host_out else "cuda"
+                tot = torch.zeros(1, dtype=torch.int64, device=dev_)
+                pv = torch.zeros(g.n, dtype=torch.int64, device=dev_)
+                if host_out:
+                    tot, pv = tot.pin_memory(), pv.pin_memory()
+                ctx.count(o, tot, pv)
+                torch.cuda.synchronize()
+                o.free()
+                assert int(tot[0]) == T
+                np.testing.assert_array_equal(pv.cpu().numpy(), t)
+    assert ctx.check() == 0
+
+
 def test_edge_list_input(ctx):
     for g in (gen.rmat(11, 16, seed=4, keep_pairs=True), gen.grid(30, 31, seed=1, keep_pairs=True),
               gen.er(1024, 8192, seed=1, keep_pairs=True)):
