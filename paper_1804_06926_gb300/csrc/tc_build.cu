@@ -471,21 +471,44 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(i
 // (and (rank(u), d+(u)) packed, so that the scatter gathers both of a
 // neighbour with one 8-byte load, and (first vector of u's colr row, d+(u)),
 // the descriptor the count kernels read for a partner u)
+// ... and the list of the rows k_sort_rows works on (kSortedMin <= d+ <=
+// kSortedMax, or d+ > warp_max), appended one global atomic per block and
+// iteration (one shared atomic per warp below it).
 __global__ void k_rows(int64_t n, const int64_t* __restrict__ rp, const unsigned* __restrict__ keep,
                        const int64_t* __restrict__ kpre, const int32_t* __restrict__ rank, int64_t* __restrict__ rpp,
                        int32_t* __restrict__ dplus, int2* __restrict__ rd2, int2* __restrict__ pd2,
-                       int* __restrict__ max_dplus) {
+                       int* __restrict__ max_dplus, int warp_max, int32_t* __restrict__ srows,
+                       unsigned* __restrict__ n_srows) {
+    __shared__ unsigned s_cnt, s_base;
     int mx = 0;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n; u += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = bits_before(keep, kpre, rp[u]);
-        rpp[u] = s;
-        if (u < n) {
-            const int d = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
-            dplus[u] = d;
-            rd2[u] = make_int2(rank[u], d);
-            pd2[u] = make_int2((int)((s + 3 * u + 3) >> 2), d);  // colr_row(rpp, u) / 4
-            mx = max(mx, d);
+    const int lane = threadIdx.x & 31;
+    // block-uniform trip count, so that every thread takes part in each append
+    for (int64_t u0 = (int64_t)blockIdx.x * blockDim.x; u0 <= n; u0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = u0 + threadIdx.x;
+        bool listed = false;
+        if (u <= n) {
+            const int64_t s = bits_before(keep, kpre, rp[u]);
+            rpp[u] = s;
+            if (u < n) {
+                const int d = (int)(bits_before(keep, kpre, rp[u + 1]) - s);
+                dplus[u] = d;
+                rd2[u] = make_int2(rank[u], d);
+                pd2[u] = make_int2((int)((s + 3 * u + 3) >> 2), d);  // colr_row(rpp, u) / 4
+                mx = max(mx, d);
+                listed = (d >= kSortedMin && d <= kSortedMax) || d > warp_max;
+            }
         }
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const unsigned m = __ballot_sync(0xffffffffu, listed);
+        const int lead = m ? __ffs(m) - 1 : 0;
+        unsigned at = 0;
+        if (m && lane == lead) at = atomicAdd(&s_cnt, (unsigned)__popc(m));
+        __syncthreads();
+        if (threadIdx.x == 0 && s_cnt) s_base = atomicAdd(n_srows, s_cnt);
+        __syncthreads();
+        at = __shfl_sync(0xffffffffu, at, lead);
+        if (listed) srows[s_base + at + __popc(m & ((1u << lane) - 1u))] = (int32_t)u;
     }
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(max_dplus, mx);
@@ -664,24 +687,20 @@ constexpr int kSortWarps = TC_SORT_WARPS;
 
 __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int64_t n, const int64_t* __restrict__ rpp,
                                                                const int32_t* __restrict__ dplus,
-                                                               const int* __restrict__ max_dplus, int warp_max,
+                                                               const int32_t* __restrict__ srows,
+                                                               const unsigned* __restrict__ n_srows,
                                                                int32_t* __restrict__ colr, int2* __restrict__ rspan) {
-    const int mdp = *max_dplus;
-    if (mdp < kSortedMin && mdp <= warp_max) return;  // no row to partition or span
+    const unsigned nl = *n_srows;  // the rows k_rows listed
+    if (nl == 0u) return;
     extern __shared__ int sbuf[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int* buf = sbuf + w * (kSortedMax + kRankLevels);
     int* cur = buf + kSortedMax;  // per level: count, then next free position
-    const int64_t nwarps = (int64_t)gridDim.x * kSortWarps;
-    for (int64_t u0 = ((int64_t)blockIdx.x * kSortWarps + w) * 32; u0 < n; u0 += nwarps * 32) {
-        const int64_t ul = u0 + lane;
-        const int dl = ul < n ? dplus[ul] : 0;
-        unsigned todo = __ballot_sync(0xffffffffu, (dl >= kSortedMin && dl <= kSortedMax) || dl > warp_max);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t u = u0 + src;
-            const int d = __shfl_sync(0xffffffffu, dl, src);
+    const unsigned nwarps = gridDim.x * kSortWarps;
+    for (unsigned li = blockIdx.x * kSortWarps + w; li < nl; li += nwarps) {  // one listed row per warp
+        {
+            const int64_t u = srows[li];
+            const int d = dplus[u];
             const bool part = d >= kSortedMin && d <= kSortedMax;
             int32_t* row = colr + colr_row(rpp, u);
             int mn = 0x7fffffff, mx = -1;
@@ -1052,6 +1071,8 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     int2* rd2 = nullptr;
     int2* pd2 = nullptr;
     unsigned long long* vtop = nullptr;
+    int32_t* srows = nullptr;     // rows for k_sort_rows, listed by k_rows
+    unsigned* n_srows = nullptr;
     void* wtmp = nullptr;
     const size_t wtb = scan_tmp_bytes(std::max(kw, std::max(uw, n)));
     auto B = [&](void** p, size_t b) {
@@ -1068,11 +1089,13 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     B((void**)&rd2, sizeof(int2) * std::max<int64_t>(n, 1));
     B((void**)&pd2, sizeof(int2) * std::max<int64_t>(n, 1));
     B((void**)&vtop, sizeof(unsigned long long) * std::max<int64_t>(n, 1));
+    B((void**)&srows, sizeof(int32_t) * std::max<int64_t>(n, 1));
+    B((void**)&n_srows, sizeof(unsigned));
     B(&wtmp, wtb);
     auto free_tmp = [&]() {
         dev_free(coord, s); dev_free(keep, s); dev_free(umask, s); dev_free(vmask, s); dev_free(wpc, s);
         dev_free(kpre, s); dev_free(upre, s); dev_free(vpre, s); dev_free(wtmp, s);
-        dev_free(rd2, s); dev_free(pd2, s); dev_free(vtop, s);
+        dev_free(rd2, s); dev_free(pd2, s); dev_free(vtop, s); dev_free(srows, s); dev_free(n_srows, s);
         dev_free(pc, s);
     };
     if (e != cudaSuccess) {
@@ -1104,8 +1127,9 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         k_popc<<<grid_for(kw, 256, ns), 256, 0, s>>>(keep, kw, wpc);
         scan_i32_to_i64(wpc, kpre, kw, wtmp, wtb, s);
         // row offsets and d+
+        cudaMemsetAsync(n_srows, 0, sizeof(unsigned), s);
         k_rows<<<grid_for(n + 1, 256, ns), 256, 0, s>>>(n, row_ptr, keep, kpre, o->rank, o->rpp, o->dplus, rd2, pd2,
-                                                        &o->dc->max_dplus);
+                                                        &o->dc->max_dplus, tun.warp_max, srows, n_srows);
         ctx->launches += 5;
     }
     {
@@ -1136,8 +1160,9 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
         PhaseScope ph(ctx, kPhRowSort, s);
         const size_t sm = sizeof(int) * (kSortedMax + kRankLevels) * kSortWarps;
         cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        const unsigned sg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kSortWarps - 1) / (32 * kSortWarps), (int64_t)ns * 32 / kSortWarps));
-        k_sort_rows<<<sg, 32 * kSortWarps, sm, s>>>(n, o->rpp, o->dplus, &o->dc->max_dplus, tun.warp_max, o->colr, o->rspan);
+        // one listed row per warp, as many warps as fit
+        const unsigned sg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + kSortWarps - 1) / kSortWarps, (int64_t)ns * 8));
+        k_sort_rows<<<sg, 32 * kSortWarps, sm, s>>>(n, o->rpp, o->dplus, srows, n_srows, o->colr, o->rspan);
         TC_LAUNCH(ctx);
     }
     // a-4: classify, group oriented edges by pivot
@@ -1170,7 +1195,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     }
     dev_free(coord, s); dev_free(keep, s); dev_free(umask, s); dev_free(vmask, s); dev_free(wpc, s);
     dev_free(kpre, s); dev_free(upre, s); dev_free(vpre, s); dev_free(wtmp, s);
-    dev_free(rd2, s); dev_free(pd2, s); dev_free(vtop, s);
+    dev_free(rd2, s); dev_free(pd2, s); dev_free(vtop, s); dev_free(srows, s); dev_free(n_srows, s);
     if (n > 0) {
         PhaseScope ph(ctx, kPhItems, s);
         k_items<<<grid_for(n, 256, ns), 256, 0, s>>>(n, o->perm, o->dplus, o->deg, tun.small_max, o->prp, tun.warp_max,
