@@ -390,6 +390,16 @@ __global__ void k_popc(const unsigned* __restrict__ mask, int64_t nw, int32_t* _
 // are padded with -1 (colr is cleared to -1 first) so that the count kernels
 // read them as whole aligned 16-byte vectors.
 // ============================================================================
+// Arrays a build kernel reads or writes once, in a stream (the input col,
+// the oriented lists while they are scattered and re-read, pcol and pdesc),
+// go through the evict-first cache operator (.cs), so that they leave L2
+// before the per-vertex arrays (deg, (rank, d+), descriptors) that the same
+// kernels gather at random.
+template <class T>
+__device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
+template <class T>
+__device__ __forceinline__ void st_stream(T* p, T v) { __stcs(p, v); }
+
 // Partition classes of an oriented edge (u, v) with a = d+(u), b = d+(v); see a-4 below.
 enum { kSkip = 0, kSmall = 1, kPivot = 2, kMerge = 3 };
 
@@ -421,7 +431,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_MIN_BLOCKS) k_orient_flags(i
 #pragma unroll
         for (int q = 0; q < kMpIpt; ++q) {
             const int e = q * kMpThreads + threadIdx.x;
-            vv[q] = e < ne ? col[j0 + e] : 0;
+            vv[q] = e < ne ? ld_stream(col + j0 + e) : 0;
         }
         if (col_copy) {  // col is the caller's pinned host array: leave a device copy for the later passes
 #pragma unroll
@@ -549,7 +559,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
             if (e < ne) {
                 const int64_t g = j0 + e;
                 kmask |= ((keep[g >> 5] >> (g & 31)) & 1u) << q;
-                vv[q] = col[g];
+                vv[q] = ld_stream(col + g);
             }
         }
         const int64_t gbase = BATCH ? tile_graph_base(c0, c1, n, row_graph, vtx_off) : 0;
@@ -620,8 +630,8 @@ __global__ void __launch_bounds__(kMpThreads, TC_MP_SCATTER_MIN_BLOCKS) k_orient
             if (valid) {
                 const int k = S.row[e];
                 if (kq) {
-                    colp[pos] = vv[q];
-                    colr[pos + 3 * (i0 + k) + 3 - S.du[k]] = rr[q];
+                    st_stream(colp + pos, vv[q]);
+                    st_stream(colr + pos + 3 * (i0 + k) + 3 - S.du[k], rr[q]);
                     // a-4 classification of the oriented edge (u, v) at position pos
                     const int a = S.cs[k], b = bb[q];
                     const int cls = edge_class(a, b, small_max, merge_ratio, merge_max);
@@ -840,7 +850,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_sc
             const bool pu = (uw[q] >> bit) & 1u, pv = (vw[q] >> bit) & 1u;  // 0 past the tile
             cu[q] = pu ? __popc(uw[q] & ((1u << bit) - 1u)) : -1;
             if (pv) pvm |= 1u << q;
-            vv[q] = (pu || pv) ? colp[g] : 0;
+            vv[q] = (pu || pv) ? ld_stream(colp + g) : 0;
         }
         int64_t dst[kMpIpt];
 #pragma unroll
@@ -855,7 +865,7 @@ __global__ void __launch_bounds__(kMpThreads, TC_PSCATTER_MIN_BLOCKS) k_pivot_sc
         for (int q = 0; q < kMpIpt; ++q) {
             if (dst[q] < 0) continue;
             const int e = q * kMpThreads + threadIdx.x;
-            pcol[dst[q]] = cu[q] >= 0 ? vv[q] : (int32_t)(i0 + S.row[e]);
+            st_stream(pcol + dst[q], cu[q] >= 0 ? vv[q] : (int32_t)(i0 + S.row[e]));
         }
         __syncthreads();
     }
@@ -868,7 +878,7 @@ __global__ void k_pdesc(const unsigned long long* __restrict__ n_pivot, const in
                         const int2* __restrict__ pd2, int2* __restrict__ pdesc) {
     const int64_t np = (int64_t)*n_pivot;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x)
-        pdesc[i] = pd2[pcol[i]];
+        st_stream(pdesc + i, pd2[ld_stream(pcol + i)]);
 }
 
 // Work items per pivot, pivots taken in descending rank order.  Warp class
