@@ -225,11 +225,14 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ r
 // ============================================================================
 // CTA work items carry this many times `chunk` partners (one table build and
 // flush serve them all).  At most 32767 partners keep the 16-bit direct cells
-// exact.  At most (2^31 - 1) / (max d+ + 3) partners keep every 32-bit direct
+// exact.  At most (2^31 - 1) / (max d+ + 15) partners keep every 32-bit direct
 // cell of the count kernel below its marker bit: a cell inside the table's
 // span gains at most one count per partner (a list holds each id once), and
-// the 32 dummy cells past the span take the probes that fall outside it,
-// padding included, at most partners x (max d+ + 3) elements in all.
+// each of the 32 dummy cells past the span belongs to one lane and takes that
+// lane's probes outside the span.  A lane probes at most its share of a
+// partner's list rounded up to whole batches of 16 elements (row padding and
+// the -1 fill past the list's start included), at most d+ + 15 per partner,
+// so at most partners x (max d+ + 15) in all.
 #ifndef TC_CTA_CHUNK_MUL
 #define TC_CTA_CHUNK_MUL 2
 #endif
@@ -971,7 +974,7 @@ tc_status build_from_device_csr(tc_ctx* ctx, int64_t n, int64_t nnz, const int64
     const int64_t chunk = tun.chunk, cap = tun.table_cap;
     const int64_t chunk_c =
         std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(chunk * TC_CTA_CHUNK_MUL, 32767),
-                                               ((int64_t(1) << 31) - 1) / (dmax + 3)));
+                                               ((int64_t(1) << 31) - 1) / (dmax + 15)));
     const int64_t chunk_min = std::min(chunk, chunk_c);  // partners of the shortest item of either list
     auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
     // warp items: sum over warp pivots of ceil(pc/chunk) <= #pivots + m/chunk
