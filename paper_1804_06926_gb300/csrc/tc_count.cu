@@ -155,6 +155,10 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 #define TC_CTA_LANE_SHIFT 5
 #endif
 constexpr int kVec = TC_CTA_VEC;  // 16-byte vector loads in flight per lane
+// the next work item's descriptors are copied ahead with cp.async
+#ifndef TC_CTA_ITEM_PREFETCH
+#define TC_CTA_ITEM_PREFETCH 1
+#endif
 
 
 // ---------------------------------------------------------------------------
@@ -606,6 +610,15 @@ constexpr long long kWaitCycles = 2000000000ll;  // about one second at 2 GHz
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// One thread's asynchronous copy of 4 or 8 bytes (aligned to their size)
+// from global into shared memory; completes at cp.async.wait_all.
+__device__ __forceinline__ void cp_async_g2s(void* sdst, const void* gsrc, int bytes) {
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
 }
@@ -918,8 +931,17 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
     // the next work item, fetched one iteration ahead by thread 0 so that the
     // queue atomic and the dependent descriptor loads overlap the current item
     __shared__ Item s_cur;
-    __shared__ long long s_r0, s_r1;
+    __shared__ long long s_r0, s_r1, s_prp;
+    __shared__ int2 s_span;
     __shared__ int s_valid;
+#if TC_CTA_ITEM_PREFETCH
+    // the next item's row offset, d+, partner offset and rank span, copied
+    // into shared memory by thread 0 with cp.async while the current item's
+    // partners are walked (no registers held, no stall until the item ends)
+    __shared__ long long s_nrpp, s_nprp;
+    __shared__ int2 s_nspan;
+    __shared__ int s_ndp;
+#endif
     const int lane = threadIdx.x & 31;
     // hash mode probes rank ids (so that a short span can use the bitmap);
     // the binary-search mode probes the id-sorted lists
@@ -937,6 +959,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
             s_cur = a.items[it];
             s_r0 = kPadded ? colr_row(a.rpp, s_cur.p) : a.rpp[s_cur.p];
             s_r1 = s_r0 + a.dp[s_cur.p];
+            s_prp = a.prp[s_cur.p];
+            s_span = a.rspan[s_cur.p];
         }
     }
     for (;;) {
@@ -944,7 +968,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
         if (!s_valid) break;
         const Item item = s_cur;
         const int p = item.p;
-        const int64_t r0 = s_r0, r1 = s_r1;
+        const int64_t r0 = s_r0, r1 = s_r1, pbase = s_prp;
+        const int2 pspan = s_span;
         __syncthreads();  // everyone has read the current item
         unsigned long long nit = 0;
         Item nitem{};
@@ -971,9 +996,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
         if (PROBE == kProbeHash && a.bitmap_bits > 0) {
             int mn, mx;
             if (r1 - r0 == len) {  // the whole row: its span is known
-                const int2 sp = a.rspan[p];
-                mn = sp.x;
-                mx = sp.y;
+                mn = pspan.x;
+                mx = pspan.y;
             } else {
                 mn = 0x7fffffff;
                 mx = -1;
@@ -1055,11 +1079,20 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
         }
         __syncthreads();
         unsigned long long acc;
-        if (mode == kModeDirect32) acc = cta_partners<PV, kModeDirect32>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
-        else if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
-        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
-        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
-        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, a.prp[p], item.pb, item.pe, pmax, sc, st);
+#if TC_CTA_ITEM_PREFETCH
+        if (threadIdx.x == 0 && nit < n_items) {
+            cp_async_g2s(&s_nrpp, a.rpp + nitem.p, 8);
+            cp_async_g2s(&s_ndp, a.dp + nitem.p, 4);
+            cp_async_g2s(&s_nprp, a.prp + nitem.p, 8);
+            cp_async_g2s(&s_nspan, a.rspan + nitem.p, 8);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+#endif
+        if (mode == kModeDirect32) acc = cta_partners<PV, kModeDirect32>(a, L, tb, pbase, item.pb, item.pe, pmax, sc, st);
+        else if (mode == kModeDirect) acc = cta_partners<PV, kModeDirect>(a, L, tb, pbase, item.pb, item.pe, pmax, sc, st);
+        else if (mode == kModeBitmap) acc = cta_partners<PV, kModeBitmap>(a, L, tb, pbase, item.pb, item.pe, pmax, sc, st);
+        else if (mode == kModeHash) acc = cta_partners<PV, kModeHash>(a, L, tb, pbase, item.pb, item.pe, pmax, sc, st);
+        else acc = cta_partners<PV, kModeBsearch>(a, L, tb, pbase, item.pb, item.pe, pmax, sc, st);
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
@@ -1122,8 +1155,19 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : (STAGED ? 3 : TC_C
             s_valid = nit < n_items;
             if (s_valid) {
                 s_cur = nitem;
+#if TC_CTA_ITEM_PREFETCH
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                const int64_t rp_n = s_nrpp;
+                s_r0 = kPadded ? colr_row_of(rp_n, nitem.p) : rp_n;
+                s_r1 = s_r0 + s_ndp;
+                s_prp = s_nprp;
+                s_span = s_nspan;
+#else
                 s_r0 = kPadded ? colr_row(a.rpp, nitem.p) : a.rpp[nitem.p];
                 s_r1 = s_r0 + a.dp[nitem.p];
+                s_prp = a.prp[nitem.p];
+                s_span = a.rspan[nitem.p];
+#endif
             }
         }
     }

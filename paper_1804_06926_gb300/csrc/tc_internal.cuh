@@ -54,9 +54,10 @@ namespace tc {
 // are 16-byte aligned and disjoint: the gap to the next start is a multiple
 // of 4 of at least d+(u), so each row has room for its padding, and no offset
 // array or scan is needed (colr holds at most m + 3n + 3 entries).
-__host__ __device__ __forceinline__ int64_t colr_row(const int64_t* rpp, int64_t u) {
-    return (rpp[u] + 3 * u + 3) & ~(int64_t)3;
+__host__ __device__ __forceinline__ int64_t colr_row_of(int64_t rpp_u, int64_t u) {
+    return (rpp_u + 3 * u + 3) & ~(int64_t)3;
 }
+__host__ __device__ __forceinline__ int64_t colr_row(const int64_t* rpp, int64_t u) { return colr_row_of(rpp[u], u); }
 // colr rows with kSortedMin <= d+(u) <= kSortedMax are partitioned by the
 // level of each rank id x, rank_level(n - x) (an eighth of an octave of the
 // distance to the top rank: non-increasing in x), into buckets of descending
