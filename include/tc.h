@@ -126,7 +126,7 @@ enum {
     TC_PH_DEGREE = 0, TC_PH_VALIDATE, TC_PH_ORIENT_COUNT, TC_PH_ORIENT_SCAN, TC_PH_ORIENT_SCATTER,
     TC_PH_PIVOT_COUNT, TC_PH_PIVOT_SCAN, TC_PH_PIVOT_SCATTER, TC_PH_ITEMS, TC_PH_COUNT_SMALL,
     TC_PH_COUNT_WARP, TC_PH_COUNT_CTA, TC_PH_EDGE_SORT, TC_PH_COUNT_INIT, TC_PH_RANK, TC_PH_ROW_SORT,
-    TC_PH_COUNT_MERGE
+    TC_PH_COUNT_MERGE, TC_PH_FUSED
 };
 typedef struct tc_trace {
     int64_t launches;                        /* kernel launches since the last read */
@@ -186,6 +186,24 @@ tc_status tc_build_oriented_csr(tc_ctx* ctx, const tc_graph* g, tc_ocsr** out, v
  * call copies the results back and synchronises `stream` before returning.
  * Any number of tc_count calls may run on one tc_ocsr, on any streams. */
 tc_status tc_count(tc_ctx* ctx, const tc_ocsr* o, int64_t* total, int64_t* per_vertex, void* stream);
+
+/* All four steps in one call, without a handle: degree and (degree, id)
+ * rank, orientation filter and compaction (Sec. 4.2.1, Alg. 2
+ * Form_Filtered_Edge_List), intersection of N+(u) and N+(v) for every oriented
+ * edge (Sec. 3.2, Alg. 2 Compute_Intersection) and the reduction (Alg. 2
+ * Reduce).  A CSR graph with at most 8192 vertices whose arrays fit one CTA's
+ * shared memory (4 * (N2 + 3n + m + 34) bytes <= 224 KiB, N2 = n rounded up to
+ * a power of two, m = nnz/2), without TC_VALIDATE, is counted by one
+ * single-CTA kernel: one launch instead of the thirty-odd of the general path,
+ * the same exact results.  Any other graph takes tc_build_oriented_csr +
+ * tc_count and releases the handle in stream order.  Inputs as in
+ * tc_build_oriented_csr (TC_IN_HOST copies them first); outputs as in tc_count
+ * (total required, per_vertex nullable; device outputs are written
+ * asynchronously, host outputs are copied back and `stream` is synchronised).
+ * The input must be a simple symmetric CSR (as for tc_build_oriented_csr
+ * without TC_VALIDATE): other input gives meaningless counts, but every index
+ * the fused kernel forms stays inside its arrays. */
+tc_status tc_count_graph(tc_ctx* ctx, const tc_graph* g, int64_t* total, int64_t* per_vertex, void* stream);
 
 /* Triangle-derived metrics, the use of the counts the paper names (Sec. 5,
  * clustering coefficient and transitivity).  With d(v) the undirected degree:

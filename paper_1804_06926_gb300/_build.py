@@ -20,7 +20,7 @@ STAMP = LIB + ".arch"
 # The TC_DEBUG build: every count kernel checks its indexes and table invariants,
 # raises a bit of the device check word (tc_check) and skips the bad access.
 DEBUG_LIB = os.path.join(HERE, "libtc_debug.so")
-SOURCES = ["tc_build.cu", "tc_count.cu", "tc_sort.cu", "tc_api.cu", "tc_serve.cu", "tc_noalloc.cu", "tc_metrics.cu", "tc_support.cu", "tc_labels.cu"]
+SOURCES = ["tc_build.cu", "tc_count.cu", "tc_sort.cu", "tc_api.cu", "tc_serve.cu", "tc_noalloc.cu", "tc_metrics.cu", "tc_support.cu", "tc_labels.cu", "tc_fused.cu"]
 HEADERS = [os.path.join(CSRC, "tc_internal.cuh"), os.path.join(ROOT, "include", "tc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

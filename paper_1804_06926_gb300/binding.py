@@ -68,7 +68,7 @@ class tc_result(C.Structure):
 
 TRACE_PHASES = ("degree", "validate", "orient_count", "orient_scan", "orient_scatter", "pivot_count",
                 "pivot_scan", "pivot_scatter", "items", "count_small", "count_warp", "count_cta", "edge_sort",
-                "count_init", "rank", "row_sort", "count_merge")
+                "count_init", "rank", "row_sort", "count_merge", "fused")
 
 
 class tc_trace(C.Structure):
@@ -94,6 +94,7 @@ _SIGS = {
     "tc_check": (C.c_int, [_vp, _P(C.c_uint32), _vp]),
     "tc_build_oriented_csr": (C.c_int, [_vp, _P(tc_graph), _P(_vp), _vp]),
     "tc_count": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "tc_count_graph": (C.c_int, [_vp, _P(tc_graph), _vp, _vp, _vp]),
     "tc_count_shard": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     "tc_clustering": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tc_edge_support": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]),
@@ -323,6 +324,17 @@ class Context:
     def count(self, o: OCSR, total=None, per_vertex=None, stream=None):
         """total / per_vertex: int64 torch tensors (device) or numpy arrays (host)."""
         _check(self, tc_count(self.handle, o.handle, _ptr(total), _ptr(per_vertex), _stream_ptr(stream)))
+        return total, per_vertex
+
+    def count_graph(self, n, row_ptr, col, total, per_vertex=None, stream=None, validate=False):
+        """Build and count in one call (tc_count_graph): a graph small enough
+        for one CTA's shared memory takes one fused kernel launch, any other the
+        build + count path.  Inputs as in build(), outputs as in count()."""
+        g = tc_graph()
+        g.n, g.nnz = int(n), int(col.shape[0])
+        g.row_ptr, g.col = _ptr(row_ptr), _ptr(col)
+        g.flags = (TC_IN_HOST if _is_host(row_ptr) else 0) | (TC_VALIDATE if validate else 0)
+        _check(self, tc_count_graph(self.handle, C.byref(g), _ptr(total), _ptr(per_vertex), _stream_ptr(stream)))
         return total, per_vertex
 
     def count_shard(self, o: OCSR, shard, nshards, total=None, per_vertex=None, stream=None):

@@ -46,7 +46,8 @@ static cudaEvent_t get_event(tc_ctx* c) {
 static const char* const kPhaseNames[kNumPhases] = {
     "tc.degree",        "tc.validate",   "tc.orient_count", "tc.orient_scan", "tc.orient_scatter", "tc.pivot_count",
     "tc.pivot_scan",    "tc.pivot_scatter", "tc.items",     "tc.count_small", "tc.count_warp",     "tc.count_cta",
-    "tc.edge_sort",     "tc.count_init", "tc.rank",         "tc.row_sort",    "tc.count_merge"};
+    "tc.edge_sort",     "tc.count_init", "tc.rank",         "tc.row_sort",    "tc.count_merge",
+    "tc.fused"};
 
 PhaseScope::PhaseScope(tc_ctx* c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
     nvtxRangePushA(id >= 0 && id < kNumPhases ? kPhaseNames[id] : "tc.phase");
@@ -381,6 +382,62 @@ tc_status tc_count_shard(tc_ctx* ctx, const tc_ocsr* o, int32_t shard, int32_t n
     if (o->G > 0) return set_err(ctx, TC_ERR_INVALID_ARG, "batch handle: use tc_count_batch");
     cudaSetDevice(o->device);
     return count_any(ctx, o, total, 1, per_vertex, (cudaStream_t)stream, shard, nshards);
+}
+
+tc_status tc_count_graph(tc_ctx* ctx, const tc_graph* g, int64_t* total, int64_t* per_vertex, void* stream) {
+    if (!ctx || !g || !total) return set_err(ctx, TC_ERR_INVALID_ARG, "null argument");
+    if (g->n < 0 || g->n > 0x7fffffffLL || g->nnz < 0)
+        return set_err(ctx, TC_ERR_INVALID_ARG, "n must be in [0, 2^31) and nnz >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaSetDevice(ctx->device);
+    const bool fused = g->row_ptr && !(g->flags & TC_VALIDATE) && g->nnz % 2 == 0 && fused_fits(g->n, g->nnz);
+    if (!fused) {  // build, count, release the handle in stream order
+        tc_ocsr* o = nullptr;
+        tc_status st = tc_build_oriented_csr(ctx, g, &o, stream);
+        if (st != TC_OK) return st;
+        st = tc_count(ctx, o, total, per_vertex, stream);
+        release_ocsr(o, s, true);
+        return st;
+    }
+    if (g->nnz > 0 && !g->col) return set_err(ctx, TC_ERR_INVALID_ARG, "col is NULL");
+    const int64_t n = g->n;
+    const int64_t* rp = g->row_ptr;
+    const int32_t* col = g->col;
+    int64_t* drp = nullptr;
+    int32_t* dcol = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (g->flags & TC_IN_HOST) {
+        if (g->row_ptr[0] != 0 || g->row_ptr[n] != g->nnz)
+            return set_err(ctx, TC_ERR_INVALID_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] must be nnz");
+        e = upload(g->row_ptr, n + 1, &drp, s);
+        if (e == cudaSuccess) e = upload(g->col, g->nnz, &dcol, s);
+        rp = drp;
+        col = dcol;
+    }
+    const bool h_tot = is_host_ptr(total);
+    const bool h_pv = per_vertex && is_host_ptr(per_vertex);
+    unsigned long long* dt = (unsigned long long*)total;
+    unsigned long long* dpv = (unsigned long long*)per_vertex;
+    if (e == cudaSuccess && h_tot) e = dev_alloc((void**)&dt, sizeof(int64_t), s);
+    if (e == cudaSuccess && h_pv) e = dev_alloc((void**)&dpv, sizeof(int64_t) * (size_t)std::max<int64_t>(n, 1), s);
+    if (e == cudaSuccess) {
+        PhaseScope ph(ctx, kPhFused, s);
+        e = launch_fused(n, g->nnz, rp, col, dt, dpv, s);
+        TC_LAUNCH(ctx);
+    }
+    if (e == cudaSuccess && h_tot) e = cudaMemcpyAsync(total, dt, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_pv && n > 0)
+        e = cudaMemcpyAsync(per_vertex, dpv, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s);
+    if (h_tot) dev_free(dt, s);
+    if (h_pv) dev_free(dpv, s);
+    dev_free(drp, s);
+    dev_free(dcol, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "fused count");
+    if (h_tot || h_pv) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "fused count: synchronise");
+    }
+    return TC_OK;
 }
 
 tc_status tc_ocsr_get_view(const tc_ocsr* o, tc_ocsr_view* out) {

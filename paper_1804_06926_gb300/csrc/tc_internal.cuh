@@ -128,7 +128,7 @@ namespace tc {
 enum Phase {
     kPhDegree = 0, kPhValidate, kPhOrientCount, kPhOrientScan, kPhOrientScatter, kPhPivotCount, kPhPivotScan,
     kPhPivotScatter, kPhItems, kPhCountSmall, kPhCountWarp, kPhCountCta, kPhEdgeSort, kPhCountInit, kPhRank,
-    kPhRowSort, kPhCountMerge, kNumPhases
+    kPhRowSort, kPhCountMerge, kPhFused, kNumPhases
 };
 
 // RAII phase marker: records an event pair on `s` when tracing is on.
@@ -178,6 +178,13 @@ tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t npairs, const int32_t* sr
 
 // Launch the count kernels.  totals: device int64 [G or 1], zeroed here.
 // shard/nshards: the launch covers that equal part of the work lists (0/1 = all).
+// tc_fused.cu: the whole method for one small graph in one single-CTA launch
+// (n <= kFusedMaxN, its arrays within kFusedMaxSmem bytes of shared memory)
+constexpr int64_t kFusedMaxN = 8192;
+constexpr int64_t kFusedMaxSmem = 224 * 1024;
+bool fused_fits(int64_t n, int64_t nnz);
+cudaError_t launch_fused(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* col, unsigned long long* total,
+                         unsigned long long* per_vertex, cudaStream_t s);
 tc_status count_device(tc_ctx* ctx, const tc_ocsr* o, unsigned long long* totals,
                        unsigned long long* per_vertex, cudaStream_t s, int shard = 0, int nshards = 1);
 
