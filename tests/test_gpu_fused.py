@@ -38,11 +38,13 @@ def dev(a):
 
 
 def fused_words(n, m):
-    """Shared-memory words of the fused kernel (key, rank, d+/t, rpp, N+, scan)."""
+    """Shared-memory words of the fused kernel (row offsets, keys, ranks, counts,
+    oriented offsets, keep bits and their prefix, N+, scan)."""
     n2 = 1
     while n2 < max(n, 1):
         n2 *= 2
-    return n2 + 3 * n + 1 + m + 33
+    w = (2 * m + 31) // 32
+    return (n + 1) + n2 + 2 * n + (n + 1) + 2 * w + m + 33
 
 
 def fits(g):
