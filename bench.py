@@ -391,9 +391,12 @@ def run_rmat_like(args, torch, binding, dev, rank, world):
         ms = float(t.item())
 
     ph = {k: v / args.steps for k, v in tr["phase_ms"].items()}
-    count_ms = ph["count_small"] + ph["count_warp"] + ph["count_cta"]
-    build_ms = sum(ph[k] for k in ("degree", "orient_count", "orient_scan", "orient_scatter", "pivot_count",
-                                   "pivot_scan", "pivot_scatter", "items"))
+    # every traced phase belongs to one of the two: the build (a-1..a-4: degree,
+    # rank sort, orientation, row partition, work partition) and the count
+    # (a-5, a-6: output init, the intersection kernels)
+    count_ms = sum(ph[k] for k in ("count_init", "count_small", "count_warp", "count_cta", "count_merge"))
+    build_ms = sum(ph[k] for k in ("degree", "validate", "rank", "orient_count", "orient_scan", "orient_scatter",
+                                   "row_sort", "pivot_count", "pivot_scan", "pivot_scatter", "items", "edge_sort"))
 
     # end to end through the public API: pinned host CSR in, host results out
     h_rp = torch.from_numpy(g.row_ptr).pin_memory()
