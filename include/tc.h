@@ -192,8 +192,8 @@ tc_status tc_count(tc_ctx* ctx, const tc_ocsr* o, int64_t* total, int64_t* per_v
  * Form_Filtered_Edge_List), intersection of N+(u) and N+(v) for every oriented
  * edge (Sec. 3.2, Alg. 2 Compute_Intersection) and the reduction (Alg. 2
  * Reduce).  A CSR graph with at most 8192 vertices whose arrays fit one CTA's
- * shared memory (4 * (N2 + 4n + m + 2W + 35) bytes <= 224 KiB, N2 = n rounded up
- * to a power of two, m = nnz/2, W = ceil(nnz/32)), without TC_VALIDATE, is counted by one
+ * shared memory (4 * (3n + m + 2W + 35) bytes <= 224 KiB, m = nnz/2,
+ * W = ceil(nnz/32)), without TC_VALIDATE, is counted by one
  * single-CTA kernel: one launch instead of the thirty-odd of the general path,
  * the same exact results.  Any other graph takes tc_build_oriented_csr +
  * tc_count and releases the handle in stream order.  Inputs as in

@@ -1,13 +1,15 @@
 // tc_fused.cu -- the whole method for one small graph in one kernel launch.
 //
-// A graph whose degree keys, ranks, oriented CSR and per-vertex counts fit in
-// one CTA's shared memory is counted by a single CTA: degrees and the
-// (degree, id) rank (Sec. 4.2.1), the orientation filter and its compaction
-// into the oriented CSR N+ (Sec. 4.2.1, Alg. 2 Form_Filtered_Edge_List), the
-// sorted-merge intersection of N+(u) and N+(v) for every oriented edge
-// (Sec. 3.2, Alg. 2 Compute_Intersection) and the reduction to T and t(v)
-// (Alg. 2 Reduce).  Such graphs are launch-bound on the general path (some
-// thirty kernels for a few thousand edges); here they take one launch.
+// A graph whose row offsets, oriented CSR and per-vertex counts fit in one
+// CTA's shared memory is counted by a single CTA: degrees and the (degree, id)
+// order (Sec. 4.2.1), the orientation filter and its compaction into the
+// oriented CSR N+ (Sec. 4.2.1, Alg. 2 Form_Filtered_Edge_List), the
+// intersection of N+(u) and N+(v) for every oriented edge (Sec. 3.2, Alg. 2
+// Compute_Intersection: a sorted merge, or for a pair of very unequal lengths
+// a search of each element of the shorter list in the longer one) and the
+// reduction to T and t(v) (Alg. 2 Reduce).  Such graphs are launch-bound on
+// the general path (some thirty kernels for a few thousand edges); here they
+// take one launch.
 #include <algorithm>
 
 #include "tc_internal.cuh"
@@ -45,19 +47,19 @@ __device__ __forceinline__ int fused_block_excl_scan(int v, int* sm, int* total)
 }
 
 // One CTA of kFusedThreads threads.  Shared memory (32-bit words): srp[n+1]
-// (row offsets), key[N2] (N2 = n rounded up to a power of two, at least 1),
-// rnk[n], tv[n] (per-vertex counts), rpp[n+1], kw[W] (one keep bit per input
-// entry, W = ceil(nnz/32)), wpre[W] (kept entries before each word), colp[m],
-// scan scratch[33].
-//   rp, col : the input CSR on the device (simple, rows ascending, n <= 2^13
-//             so that (degree << idbits) | id fits 32 bits).
+// (row offsets, so d(v) = srp[v+1] - srp[v]), tv[n] (per-vertex counts),
+// rpp[n+1], kw[W] (one keep bit per input entry, W = ceil(nnz/32)), wpre[W]
+// (kept entries before each word), colp[m], scan scratch[33].
+//   rp, col : the input CSR on the device (simple, rows ascending).
 //   total   : T; per_vertex (nullable): t(v) for v < n.  Both overwritten.
-// The input entries are walked in coalesced runs (one warp = 32 consecutive
-// entries = one keep word), so the loads of the whole CSR are in flight at
-// once; kept entries keep their input order, so an entry's place in N+ is the
-// number of kept entries before it (wpre plus a popcount), as in the build.
+// The orientation needs only the comparison (d(u), u) < (d(v), v), so no rank
+// is formed.  The input entries are walked in coalesced runs (one warp = 32
+// consecutive entries = one keep word), so the loads of the whole CSR are in
+// flight at once; kept entries keep their input order, so an entry's place in
+// N+ is the number of kept entries before it (wpre plus a popcount), as in
+// the build.
 constexpr int kFusedRun = 8;  // keep words per warp and step (loads in flight per lane)
-__global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int N2, int idbits, int nnz, int m,
+__global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int nnz, int m,
                                                                const int64_t* __restrict__ rp,
                                                                const int32_t* __restrict__ col,
                                                                unsigned long long* __restrict__ total,
@@ -65,9 +67,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int N2, in
     extern __shared__ __align__(16) unsigned fsm[];
     const int W = (nnz + 31) >> 5;
     int* srp = reinterpret_cast<int*>(fsm);
-    unsigned* key = reinterpret_cast<unsigned*>(srp + n + 1);
-    int* rnk = reinterpret_cast<int*>(key + N2);
-    int* tv = rnk + n;
+    int* tv = srp + n + 1;
     int* rpp = tv + n;
     unsigned* kw = reinterpret_cast<unsigned*>(rpp + n + 1);
     int* wpre = reinterpret_cast<int*>(kw + W);
@@ -82,30 +82,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int N2, in
     for (int i = tid; i < m; i += nt) colp[i] = 0;
     for (int v = tid; v <= n; v += nt) srp[v] = (int)min(max(rp[v], (int64_t)0), (int64_t)nnz);
     __syncthreads();
-    // degrees and (degree, id) keys; padding sorts last
-    for (int v = tid; v < N2; v += nt)
-        key[v] = v < n ? ((unsigned)(srp[v + 1] - srp[v]) << idbits) | (unsigned)v : 0xffffffffu;
-    __syncthreads();
-    // bitonic sort of the keys, ascending: key[i] = the vertex of rank i
-    for (int k = 2; k <= N2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < N2; i += nt) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned a = key[i], b = key[ixj];
-                    if ((a > b) == ((i & k) == 0)) {
-                        key[i] = b;
-                        key[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    const unsigned idmask = (1u << idbits) - 1u;
-    for (int i = tid; i < n; i += nt) rnk[key[i] & idmask] = i;
-    __syncthreads();
-    // orientation filter: entry j of row u is kept iff rank(u) < rank(col[j])
+    // orientation filter: entry j of row u is kept iff (d(u), u) < (d(v), v), v = col[j]
     for (int w0 = warp * kFusedRun; w0 < W; w0 += nw * kFusedRun) {
         int vv[kFusedRun];
 #pragma unroll
@@ -125,7 +102,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int N2, in
                     if (srp[mid] <= j) lo = mid;
                     else hi = mid;
                 }
-                kp = rnk[vv[q]] > rnk[lo];
+                const int v = vv[q];
+                const int du = srp[lo + 1] - srp[lo], dv = srp[v + 1] - srp[v];
+                kp = dv > du || (dv == du && v > lo);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, kp);
             if (lane == 0) kw[w0 + q] = bal;
@@ -183,18 +162,45 @@ __global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int N2, in
         }
         const int u = lo, v = colp[e];
         int a = rpp[u], ae = rpp[u + 1], b = rpp[v], be = rpp[v + 1];
+        if (ae - a > be - b) {  // [a, ae) the shorter list, [b, be) the longer
+            const int t0 = a, t1 = ae;
+            a = b;
+            ae = be;
+            b = t0;
+            be = t1;
+        }
         unsigned c = 0;
-        while (a < ae && b < be) {
-            const int x = colp[a], y = colp[b];
-            if (x == y) {
-                atomicAdd(reinterpret_cast<unsigned*>(&tv[x]), 1u);
-                ++c;
-                ++a;
-                ++b;
-            } else if (x < y) {
-                ++a;
-            } else {
-                ++b;
+        if (8 * (ae - a) < be - b) {
+            // skewed pair: each element of the shorter list is searched in the
+            // rest of the longer one (both ascending)
+            for (; a < ae && b < be; ++a) {
+                const int x = colp[a];
+                int l = b, h = be;
+                while (l < h) {
+                    const int mid = (l + h) >> 1;
+                    if (colp[mid] < x) l = mid + 1;
+                    else h = mid;
+                }
+                if (l < be && colp[l] == x) {
+                    atomicAdd(reinterpret_cast<unsigned*>(&tv[x]), 1u);
+                    ++c;
+                    ++l;
+                }
+                b = l;
+            }
+        } else {
+            while (a < ae && b < be) {
+                const int x = colp[a], y = colp[b];
+                if (x == y) {
+                    atomicAdd(reinterpret_cast<unsigned*>(&tv[x]), 1u);
+                    ++c;
+                    ++a;
+                    ++b;
+                } else if (x < y) {
+                    ++a;
+                } else {
+                    ++b;
+                }
             }
         }
         if (c) {
@@ -211,19 +217,12 @@ __global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int N2, in
         for (int u = tid; u < n; u += nt) per_vertex[u] = (unsigned long long)(unsigned)tv[u];
 }
 
-static int fused_pow2(int x) {
-    int p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
-
 // Shared-memory bytes of the fused kernel for n vertices and m oriented edges
 // (-1 when the graph is outside its limits).
 static int64_t fused_smem_bytes(int64_t n, int64_t m) {
     if (n < 0 || n > kFusedMaxN || m < 0) return -1;
-    const int64_t N2 = fused_pow2((int)std::max<int64_t>(n, 1));
     const int64_t W = (2 * m + 31) / 32;
-    const int64_t words = (n + 1) + N2 + 2 * n + (n + 1) + 2 * W + m + 33;
+    const int64_t words = (n + 1) + n + (n + 1) + 2 * W + m + 33;
     return 4 * words;
 }
 
@@ -237,13 +236,9 @@ cudaError_t launch_fused(int64_t n, int64_t nnz, const int64_t* rp, const int32_
     const int64_t m = nnz / 2;
     const int64_t bytes = fused_smem_bytes(n, m);
     if (bytes < 0 || bytes > kFusedMaxSmem) return cudaErrorInvalidValue;
-    const int N2 = fused_pow2((int)std::max<int64_t>(n, 1));
-    int idbits = 1;
-    while ((int64_t(1) << idbits) < n) ++idbits;
     cudaError_t e = cudaFuncSetAttribute(k_count_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_count_fused<<<1, kFusedThreads, (size_t)bytes, s>>>((int)n, N2, idbits, (int)nnz, (int)m, rp, col, total,
-                                                           per_vertex);
+    k_count_fused<<<1, kFusedThreads, (size_t)bytes, s>>>((int)n, (int)nnz, (int)m, rp, col, total, per_vertex);
     return cudaGetLastError();
 }
 

@@ -38,13 +38,10 @@ def dev(a):
 
 
 def fused_words(n, m):
-    """Shared-memory words of the fused kernel (row offsets, keys, ranks, counts,
-    oriented offsets, keep bits and their prefix, N+, scan)."""
-    n2 = 1
-    while n2 < max(n, 1):
-        n2 *= 2
+    """Shared-memory words of the fused kernel (row offsets, counts, oriented
+    offsets, keep bits and their prefix, N+, scan)."""
     w = (2 * m + 31) // 32
-    return (n + 1) + n2 + 2 * n + (n + 1) + 2 * w + m + 33
+    return (n + 1) + n + (n + 1) + 2 * w + m + 33
 
 
 def fits(g):
@@ -154,10 +151,10 @@ def test_without_per_vertex(ctx):
 
 def test_limits_fall_back(ctx):
     # just over the vertex limit, and over the shared-memory limit: general path
-    for g in (gen.er(8193, 20000, seed=1), gen.rmat(12, 16, seed=1)):
+    for g in (gen.er(8193, 20000, seed=1), gen.rmat(13, 16, seed=1)):
         assert not fits(g)
         assert check(ctx, g) > 1
-    # largest vertex count the kernel takes, with ids using all 13 bits
+    # the largest vertex count the kernel takes
     g = gen.er(8192, 12000, seed=2)
     assert fits(g)
     assert check(ctx, g) == 1
