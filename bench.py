@@ -467,9 +467,10 @@ def run_rmat_like(args, torch, binding, dev, rank, world):
         fms = ev0.elapsed_time(ev1) / args.steps
         assert int(ftot.item()) == T_gpu and torch.equal(fpv, pv)
         one_call = {"ms_per_step": fms, "edges_per_s": g.m / (fms * 1e-3), "launches_per_step": fl,
-                    "how": "tc_count_graph: degree, rank, orientation, compaction, intersection and "
-                           "reduction in one call; one fused single-CTA kernel when the graph fits its "
-                           "shared memory, else build + count"}
+                    "how": "tc_count_graph: degree, (degree, id) order, orientation, compaction, "
+                           "intersection and reduction in one call; one fused kernel launch when the graph "
+                           "fits one CTA's shared memory (every CTA orients it, each counts its share of "
+                           "the edges), else build + count"}
 
     peak, peak_kind = peaks()
     cfg = ctx.get_config()

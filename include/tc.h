@@ -193,9 +193,11 @@ tc_status tc_count(tc_ctx* ctx, const tc_ocsr* o, int64_t* total, int64_t* per_v
  * edge (Sec. 3.2, Alg. 2 Compute_Intersection) and the reduction (Alg. 2
  * Reduce).  A CSR graph with at most 8192 vertices whose arrays fit one CTA's
  * shared memory (4 * (3n + m + 2W + 35) bytes <= 224 KiB, m = nnz/2,
- * W = ceil(nnz/32)), without TC_VALIDATE, is counted by one
- * single-CTA kernel: one launch instead of the thirty-odd of the general path,
- * the same exact results.  Any other graph takes tc_build_oriented_csr +
+ * W = ceil(nnz/32)), without TC_VALIDATE, is counted by one kernel
+ * launch of ceil(m/1024) CTAs of 1024 threads (at most one per SM), each CTA
+ * orienting the whole graph in its own shared memory and counting its share
+ * of the oriented edges, instead of the thirty-odd launches of the general
+ * path, with the same exact results.  Any other graph takes tc_build_oriented_csr +
  * tc_count and releases the handle in stream order.  Inputs as in
  * tc_build_oriented_csr (TC_IN_HOST copies them first); outputs as in tc_count
  * (total required, per_vertex nullable; device outputs are written

@@ -1,7 +1,7 @@
 // tc_fused.cu -- the whole method for one small graph in one kernel launch.
 //
 // A graph whose row offsets, oriented CSR and per-vertex counts fit in one
-// CTA's shared memory is counted by a single CTA: degrees and the (degree, id)
+// CTA's shared memory is counted by one kernel launch: degrees and the (degree, id)
 // order (Sec. 4.2.1), the orientation filter and its compaction into the
 // oriented CSR N+ (Sec. 4.2.1, Alg. 2 Form_Filtered_Edge_List), the
 // intersection of N+(u) and N+(v) for every oriented edge (Sec. 3.2, Alg. 2
@@ -9,7 +9,8 @@
 // a search of each element of the shorter list in the longer one) and the
 // reduction to T and t(v) (Alg. 2 Reduce).  Such graphs are launch-bound on
 // the general path (some thirty kernels for a few thousand edges); here they
-// take one launch.
+// take one launch of ceil(m/1024) CTAs, each of which orients the whole graph
+// in its shared memory and counts its share of the oriented edges.
 #include <algorithm>
 
 #include "tc_internal.cuh"
@@ -51,8 +52,11 @@ __device__ __forceinline__ int fused_block_excl_scan(int v, int* sm, int* total)
 // rpp[n+1], kw[W] (one keep bit per input entry, W = ceil(nnz/32)), wpre[W]
 // (kept entries before each word), colp[m], scan scratch[33].
 //   rp, col : the input CSR on the device (simple, rows ascending).
-//   total   : T; per_vertex (nullable): t(v) for v < n.  Both overwritten.
-// The orientation needs only the comparison (d(u), u) < (d(v), v), so no rank
+//   total   : T; per_vertex (nullable): t(v) for v < n.  Both zeroed by the
+//             host before the launch; every CTA adds its share.
+// Every CTA of the grid orients and compacts the whole graph into its own
+// shared memory (cheap at these sizes, and it needs no grid-wide barrier),
+// then takes its share of the oriented edges.  The orientation needs only the comparison (d(u), u) < (d(v), v), so no rank
 // is formed.  The input entries are walked in coalesced runs (one warp = 32
 // consecutive entries = one keep word), so the loads of the whole CSR are in
 // flight at once; kept entries keep their input order, so an entry's place in
@@ -150,10 +154,11 @@ __global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int nnz, i
     }
     __syncthreads();
     // intersection: one thread per oriented edge (u, v), a sorted merge of
-    // N+(u) and N+(v); every common w closes the triangle (u, v, w)
+    // N+(u) and N+(v); every common w closes the triangle (u, v, w).  The
+    // CTAs of the grid share the edges (each has built the same N+ above).
     unsigned long long acc = 0;
     const int me = rpp[n];
-    for (int e = tid; e < me; e += nt) {
+    for (int e = blockIdx.x * nt + tid; e < me; e += gridDim.x * nt) {
         int lo = 0, hi = n;  // the row u with rpp[u] <= e < rpp[u+1]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -212,9 +217,13 @@ __global__ void __launch_bounds__(kFusedThreads) k_count_fused(int n, int nnz, i
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0 && acc) atomicAdd(&s_T, acc);
     __syncthreads();
-    if (tid == 0) *total = s_T;
+    // this CTA's share of T and t(v), added to the outputs the host zeroed
+    if (tid == 0 && s_T) atomicAdd(total, s_T);
     if (per_vertex)
-        for (int u = tid; u < n; u += nt) per_vertex[u] = (unsigned long long)(unsigned)tv[u];
+        for (int u = tid; u < n; u += nt) {
+            const unsigned c = (unsigned)tv[u];
+            if (c) atomicAdd(&per_vertex[u], (unsigned long long)c);
+        }
 }
 
 // Shared-memory bytes of the fused kernel for n vertices and m oriented edges
@@ -236,9 +245,18 @@ cudaError_t launch_fused(int64_t n, int64_t nnz, const int64_t* rp, const int32_
     const int64_t m = nnz / 2;
     const int64_t bytes = fused_smem_bytes(n, m);
     if (bytes < 0 || bytes > kFusedMaxSmem) return cudaErrorInvalidValue;
+    int dev = 0, num_sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    // one CTA (one SM) per 1024 oriented edges: each CTA then merges about
+    // one edge per thread
+    const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(num_sms, 1), (m + kFusedThreads - 1) / kFusedThreads));
     cudaError_t e = cudaFuncSetAttribute(k_count_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess && per_vertex && n > 0)
+        e = cudaMemsetAsync(per_vertex, 0, sizeof(unsigned long long) * (size_t)n, s);
     if (e != cudaSuccess) return e;
-    k_count_fused<<<1, kFusedThreads, (size_t)bytes, s>>>((int)n, (int)nnz, (int)m, rp, col, total, per_vertex);
+    k_count_fused<<<ctas, kFusedThreads, (size_t)bytes, s>>>((int)n, (int)nnz, (int)m, rp, col, total, per_vertex);
     return cudaGetLastError();
 }
 

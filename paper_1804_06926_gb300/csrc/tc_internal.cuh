@@ -178,8 +178,9 @@ tc_status edges_to_csr(tc_ctx* ctx, int64_t n, int64_t npairs, const int32_t* sr
 
 // Launch the count kernels.  totals: device int64 [G or 1], zeroed here.
 // shard/nshards: the launch covers that equal part of the work lists (0/1 = all).
-// tc_fused.cu: the whole method for one small graph in one single-CTA launch
-// (n <= kFusedMaxN, its arrays within kFusedMaxSmem bytes of shared memory)
+// tc_fused.cu: the whole method for one small graph in one kernel launch
+// (n <= kFusedMaxN, its arrays within kFusedMaxSmem bytes of one CTA's shared
+// memory; every CTA of the launch holds the whole oriented graph)
 constexpr int64_t kFusedMaxN = 8192;
 constexpr int64_t kFusedMaxSmem = 224 * 1024;
 bool fused_fits(int64_t n, int64_t nnz);
