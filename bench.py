@@ -181,6 +181,14 @@ def peaks():
 
 COUNT_SOURCES = ("paper_1804_06926_gb300/csrc/tc_count.cu", "paper_1804_06926_gb300/csrc/tc_internal.cuh")
 
+# Every traced phase of a build + count step belongs to one of the two parts:
+# the build (a-1..a-4: degree, rank sort, orientation, row partition, work
+# partition) and the count (a-5, a-6: output init, the intersection kernels).
+# "fused" is the one-call kernel, which does both and is timed on its own.
+BUILD_PHASES = ("degree", "validate", "rank", "orient_count", "orient_scan", "orient_scatter", "row_sort",
+                "pivot_count", "pivot_scan", "pivot_scatter", "items", "edge_sort")
+COUNT_PHASES = ("count_init", "count_small", "count_warp", "count_cta", "count_merge")
+
 
 def code_digest(paths=COUNT_SOURCES):
     """First 16 hex digits of sha256 over the code of the count kernels' sources
@@ -391,12 +399,8 @@ def run_rmat_like(args, torch, binding, dev, rank, world):
         ms = float(t.item())
 
     ph = {k: v / args.steps for k, v in tr["phase_ms"].items()}
-    # every traced phase belongs to one of the two: the build (a-1..a-4: degree,
-    # rank sort, orientation, row partition, work partition) and the count
-    # (a-5, a-6: output init, the intersection kernels)
-    count_ms = sum(ph[k] for k in ("count_init", "count_small", "count_warp", "count_cta", "count_merge"))
-    build_ms = sum(ph[k] for k in ("degree", "validate", "rank", "orient_count", "orient_scan", "orient_scatter",
-                                   "row_sort", "pivot_count", "pivot_scan", "pivot_scatter", "items", "edge_sort"))
+    count_ms = sum(ph[k] for k in COUNT_PHASES)
+    build_ms = sum(ph[k] for k in BUILD_PHASES)
 
     # end to end through the public API: pinned host CSR in, host results out
     h_rp = torch.from_numpy(g.row_ptr).pin_memory()

@@ -28,3 +28,15 @@ def test_reference_arm_prints_one_complete_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_build_and_count_phases_cover_the_trace():
+    """build_ms and count_ms together cover every traced phase of a step, once."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    from paper_1804_06926_gb300 import binding
+    build, count = set(bench.BUILD_PHASES), set(bench.COUNT_PHASES)
+    assert not build & count
+    assert build | count | {"fused"} == set(binding.TRACE_PHASES)
